@@ -1,0 +1,423 @@
+"""Benchmark: all-pairs binary MI throughput (pairs/s) at the paper scale.
+
+Workload: m = 100,000 samples x n = 10,000 variables, p_j ~ Beta(0.5, 5)
+(about 91% zeros, standing in for the paper's 90%-sparse simulated data),
+1% of the columns planted as noisy copies of others.  One step = one
+mi_all_pairs call through the C ABI (pack + column terms + fused tcgen05 Gram
+with the MI epilogue), X already resident in HBM.  The input (1.0 GB) and
+the output (0.4 GB) are both larger than L2, so no flush is needed between
+steps.  Pairs per step = n(n-1)/2 (distinct unordered pairs; the diagonal is
+computed too but not counted).
+
+The JSON line also carries the plain unfused path (Gram -> int32 counts in
+HBM -> elementwise MI) and the popcount path on the same input, the roofline
+of the dominant kernel, SM clocks sampled during the timed region, an
+end-to-end figure through the host-buffer C-ABI call, and the FP64 oracle
+timed on the host cores on a bounded sample of pairs.
+
+--impl reference times the FP64 oracle (the only reference this method has:
+the paper ships no GPU code) on the host cores, each step a bounded sample of
+the same workload's pairs.
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload (weak
+scaling, no collective on the data path); value = all ranks' pairs / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PAPER_OPT_T_S = 5.6      # Opt-T (PyTorch, Apple M2 CPU) at 100000 x 10000, Fig. 2 text
+METRIC = "MI pairs/s"
+UNIT = "pairs/s"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _workload(m, n):
+    return {"workload": f"paper-scale all-pairs MI, m={m} samples x n={n} variables, "
+                        "p_j~Beta(0.5,5), 1% planted noisy copies",
+            "m": m, "n": n, "pairs_per_step": n * (n - 1) // 2,
+            "l2": "inputs larger than L2 (X 1.0 GB, out 0.4 GB per step); no flush",
+            "parallelism": "replicas (one independent problem per GPU)"}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", 0.0)),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons in a background process."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.t is not None:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- profile summary
+def _source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_19702_gb300", "csrc")
+    for f in ("gram_tc.cu", "ptx.cuh", "mi_device.cuh", "internal.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the fused Gram kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "gram_tc_fused_mi_paper_scale.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None, None
+    src = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not src or not tr:
+        return None, None
+    if src.group(1) != _source_digest():
+        return None, "stale"
+    return float(tr.group(1)), "ncu"
+
+
+# --------------------------------------------------------------- oracle timing
+def _oracle_rate(XT, n, seconds, seed=11, min_pairs=64):
+    """Oracle pairs/s on seeded pairs of the transposed data, about `seconds` of work."""
+    import oracle
+    import simdata
+    pi, pj = simdata.sample_pairs(n, n, min_pairs, seed)
+    t0 = time.perf_counter()
+    oracle.mi_pairs_t(XT, XT, pi, pj)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = min_pairs / dt
+    k = int(max(min_pairs, rate * seconds))
+    pi, pj = simdata.sample_pairs(n, n, k, seed + 1)
+    t0 = time.perf_counter()
+    oracle.mi_pairs_t(XT, XT, pi, pj)
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt
+
+
+def run_reference(args):
+    """The FP64 oracle as the reference arm, on the host cores."""
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    if rank != 0:
+        return 0
+    import oracle
+    import simdata
+    m, n = args.m, args.n
+    X, _ = simdata.make(m, n, simdata.PAPER.seed, "beta", 0.01, 0.05, device="cpu")
+    XT = oracle.transpose(X)
+    del X
+    cores = oracle.max_threads()
+    # size each step so the whole run stays within about a minute
+    rate, _, _ = _oracle_rate(XT, n, 0.5)
+    steps = args.steps + args.warmup
+    per_step = int(max(32, min(rate * 60.0 / max(steps, 1), rate * 2.0)))
+    total_pairs, total_t = 0, 0.0
+    for s in range(steps):
+        pi, pj = simdata.sample_pairs(n, n, per_step, 1000 + s)
+        t0 = time.perf_counter()
+        oracle.mi_pairs_t(XT, XT, pi, pj)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            total_pairs += per_step
+            total_t += dt
+    value = total_pairs / total_t
+    ms_per_step = 1000.0 * total_t / max(args.steps, 1)
+    sample = (f"{per_step} seeded pairs of the m={m} x n={n} workload per step "
+              f"(each pair walks all {m} samples); transposition of X excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / (n * (n - 1) / 2 / PAPER_OPT_T_S), "dtype": "f64",
+            "data": "synthetic", "config": _workload(m, n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    import simdata
+    from paper_2411_19702_gb300 import gbmi
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    gbmi.load()
+    m, n = args.m, args.n
+    pairs = n * (n - 1) // 2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    X, info = simdata.make(m, n, simdata.PAPER.seed + rank, "beta", 0.01, 0.05, device=str(dev))
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(path="fused"):
+        gbmi.mi_all_pairs(X, out=out, path=path)
+
+    def timed(path, steps, warmup, sample_clocks=False, profile=False):
+        for _ in range(warmup):
+            step(path)
+        gbmi.sync()
+        barrier()
+        torch.cuda.synchronize(dev)
+        if profile:
+            gbmi.profile(enable=True, reset=True)
+        launches0 = gbmi.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+            if uuid and not uuid.startswith("GPU-"):
+                uuid = "GPU-" + uuid
+        except Exception:
+            uuid = None
+        sampler = ClockSampler(uuid) if sample_clocks else None
+        if sampler:
+            sampler.__enter__()
+            time.sleep(0.3)
+        e0.record(stream)
+        for _ in range(steps):
+            step(path)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.__exit__(None, None, None)
+        gbmi.sync()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        prof = gbmi.profile(enable=False) if profile else None
+        return {"ms": ms, "launches": gbmi.launch_count() - launches0,
+                "clocks": sampler.summary() if sampler else None, "profile": prof}
+
+    # correctness gate on this input before timing: sampled pairs vs the oracle
+    parity = None
+    XT = None
+    if rank == 0 and not args.skip_oracle:
+        import oracle
+        step("fused")
+        gbmi.sync()
+        XT = oracle.transpose(X.cpu().numpy())
+        pi, pj = simdata.sample_pairs(n, n, 2000, 99)
+        tg, sr = info["planted_targets"], info["planted_sources"]
+        pi = np.concatenate([pi, np.minimum(tg, sr)])
+        pj = np.concatenate([pj, np.maximum(tg, sr)])
+        _, want = oracle.mi_pairs_t(XT, XT, pi, pj)
+        got = out[torch.from_numpy(pi).to(dev), torch.from_numpy(pj).to(dev)].double().cpu()
+        err = float(np.max(np.abs(got.numpy() - want)))
+        parity = {"pairs": int(len(pi)), "max_abs_err_vs_oracle": err, "tolerance": 1e-6,
+                  "ok": err <= 1e-6}
+
+    fused = timed("fused", args.steps, args.warmup, sample_clocks=True, profile=False)
+    fused_ms = max_over_ranks(fused["ms"])
+    # the same loop again with the event profiler on: per-kernel device times
+    prof = timed("fused", max(3, min(args.steps, 20)), 1, profile=True)["profile"]
+    plain = timed("plain", max(3, min(args.steps, 20)), 2)
+    popc_steps = max(1, min(args.steps, 3))
+    popc = timed("popcount", popc_steps, 1)
+
+    # roofline of the dominant kernel (tensor-bound): m*n^2/2 MACs = m*n^2 flops per launch
+    peaks = _peaks()
+    gram = prof.get("gram_tc_fused_mi", {"ms": float("nan"), "launches": 1})
+    gram_ms = gram["ms"] / max(gram["launches"], 1)
+    flops = float(m) * n * n
+    achieved = flops / (gram_ms * 1e-3) / 1e12
+    peak = 2.0 * peaks["bf16_tflops"]           # FP8 = 2 x measured BF16 (nominal ratio)
+    traffic, tsrc = _profiled_traffic()
+    step_total = sum(v["ms"] for v in prof.values())
+    kernels = {k: {"ms_per_launch": v["ms"] / max(v["launches"], 1),
+                   "launches": v["launches"],
+                   "share": v["ms"] / step_total if step_total > 0 else None}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # end to end through the host-buffer C-ABI call (pinned buffers)
+    e2e = None
+    if not args.skip_e2e:
+        Xh = X.cpu().pin_memory()
+        outh = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        gbmi.mi_all_pairs_host(Xh, outh)
+        e2e_steps = max(2, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            gbmi.mi_all_pairs_host(Xh, outh)
+        dt = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+        e2e = {"value": world * pairs / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": int(m) * n, "d2h_bytes_per_step": int(n) * n * 4}
+
+    # FP64 oracle on the host cores, bounded sample (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_oracle:
+        import oracle
+        rate, k, dt = _oracle_rate(XT, n, args.oracle_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"{k} seeded pairs of this workload in {dt:.1f} s (each pair walks all "
+                         f"{m} samples; FP64, OpenMP over pairs); transposition of X excluded"}
+
+    value = world * pairs / (fused_ms * 1e-3)
+    plain_ms = max_over_ranks(plain["ms"])
+    popc_ms = max_over_ranks(popc["ms"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": fused_ms,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / (pairs / PAPER_OPT_T_S),
+        "dtype": "e4m3", "data": "synthetic",
+        "config": dict(_workload(m, n), path="fused",
+                       arithmetic="FP8 E4M3 0/1 operands, FP32 tensor-core accumulation "
+                                  "(exact counts), FP32 epilogue, FP64 combine below 1e-4"),
+        "plain": {"value": world * pairs / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                  "path": "tcgen05 Gram -> int32 N11 in HBM -> elementwise MI kernel"},
+        "popcount": {"value": world * pairs / (popc_ms * 1e-3), "ms_per_step": popc_ms},
+        "fused_over_plain": plain_ms / fused_ms,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "gram_tc_fused_mi",
+                     "peak_source": f"{peaks['source']} bf16 burst x 2 (FP8/BF16 nominal ratio)",
+                     "flops_per_launch": flops, "ms_per_launch": gram_ms,
+                     "traffic_source": tsrc},
+        "kernels": kernels,
+        "clocks": fused["clocks"],
+        "gpu_launches": int(fused["launches"]),
+        "parity": parity,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=100_000)
+    ap.add_argument("--n", type=int, default=10_000)
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-oracle", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * gbmi — all-pairs mutual information of binary variables on GB300 (sm_103a).
+ *
+ * C ABI of libgbmi.so.  The method is the matrix formulation of arXiv
+ * 2411.19702 ("Fast Mutual Information Computation for Large Binary
+ * Datasets"):
+ *   - one co-occurrence Gram N11 = X^T X (Sec. 2 step 2, G11),
+ *   - the other three contingency counts derived from the column counts v and
+ *     the number of samples m (Sec. 3.1, Eq. 6 and Eq. 7: N01 = v_j - N11,
+ *     N10 = v_i - N11, N00 = m - v_i - v_j + N11),
+ *   - marginals from the diagonal / column counts (Sec. 2 step 3),
+ *   - MI per pair in bits from the four cells (Eq. 1 written out as Eq. 2),
+ *     with the limit 0*log 0 = 0 in place of the paper's unspecified epsilon.
+ *
+ * Conventions shared by every call:
+ *   - X (and Y) are caller-owned DEVICE pointers on the current CUDA device:
+ *     uint8, row-major, m rows (samples) by n columns (variables), leading
+ *     dimension = number of columns, no alignment requirement.  An entry is
+ *     read as 1 when its byte is non-zero (binary data, Sec. 2 step 1).
+ *   - Outputs are caller-owned device pointers, row-major, fully overwritten.
+ *   - m = samples, n = variables (the paper calls the data matrix n x m with the
+ *     letters swapped; this header always uses m for samples).
+ *   - Limits: 1 <= m <= 2^31 - 1, 1 <= n; outputs must not overlap inputs.
+ *   - Work is enqueued on the library's current stream (gbmi_set_stream) and
+ *     the calls return without waiting for it.  The returned status covers
+ *     argument checks, workspace allocation and launch errors.  A device-side
+ *     wait that times out (every wait inside the kernels is bounded) sets a
+ *     device error word that gbmi_sync() reports as GBMI_ERR_TIMEOUT.
+ *   - The library owns a grow-only device workspace (packed operands, column
+ *     counts, the n*log2(n) table); gbmi_shutdown() frees it.  Calls from
+ *     several host threads must be serialised by the caller.
+ */
+#ifndef GBMI_H_
+#define GBMI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBMI_OK = 0,
+    GBMI_ERR_ARG = 1,          /* bad argument (null pointer, size out of range, overlap) */
+    GBMI_ERR_OOM = 2,          /* workspace allocation failed */
+    GBMI_ERR_CUDA = 3,         /* a CUDA runtime/driver call or kernel launch failed */
+    GBMI_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up (reported by gbmi_sync) */
+    GBMI_ERR_NOT_BINARY = 5,   /* validation found an entry other than 0 or 1 */
+    GBMI_ERR_UNSUPPORTED = 6   /* no GPU of compute capability 10.3 (sm_103a) */
+} gbmi_status;
+
+/* Computation paths.  AUTO picks the fused tensor-core path, or the popcount
+ * path for tiny shapes, or the plain path when m is beyond the fused path's
+ * exact-count limit. */
+typedef enum {
+    GBMI_PATH_AUTO = 0,
+    GBMI_PATH_FUSED = 1,     /* tcgen05 FP8 Gram with the MI epilogue fused (one pass)      */
+    GBMI_PATH_PLAIN = 2,     /* tcgen05 FP8 Gram -> int32 N11 in HBM, then elementwise MI   */
+    GBMI_PATH_POPCOUNT = 3   /* bit-packed AND + popcount Gram (exactness cross-check)      */
+} gbmi_path;
+
+/* Options for gbmi_set_option. */
+typedef enum {
+    GBMI_OPT_FIXUP = 1,          /* 1 (default): FP64 n*log2(n) combine for pairs whose FP32 MI < 1e-4 */
+    GBMI_OPT_TIMEOUT_NS = 2,     /* bound of every device-side wait, ns (default 2e9)            */
+    GBMI_OPT_DEBUG_FLAGS = 3,    /* test hooks; 1 = the fused kernel's loader issues no copies,
+                                    so its consumer's bounded wait must run out (default 0)      */
+    GBMI_OPT_GROUP_COLS = 4,     /* tile-order group width in 256-column blocks (default 8)      */
+    GBMI_OPT_MAX_CTAS = 5,       /* cap on persistent CTAs, 0 = one per SM (default 0)           */
+    GBMI_OPT_PROFILE = 6         /* 1: time every kernel launch with CUDA events (default 0)     */
+} gbmi_option;
+
+/* ---------------------------------------------------------------- core calls */
+
+/* MI of every pair of columns of X: out[i*n + j] = MI(X_i; X_j) in bits, FP32,
+ * n x n.  The matrix is symmetric (out[i*n+j] and out[j*n+i] are the same
+ * bits) and its diagonal is the entropy of each column.
+ * Defined by Eq. 1 over all column pairs (Sec. 1, Sec. 2 steps 1-5); computed
+ * with one Gram (Sec. 3.1, Eq. 4-7).  Accuracy: counts are exact; MI is within
+ * 1e-6 absolute of the exact value. */
+gbmi_status mi_all_pairs(const uint8_t* X, int64_t m, int64_t n, float* out);
+
+/* MI between the columns of two datasets over the same m samples:
+ * out[i*n2 + j] = MI(X_i; Y_j), n1 x n2, FP32 bits.  X is m x n1, Y is m x n2.
+ * Same method with N11 = X^T Y and the column counts of each input. */
+gbmi_status mi_cross(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
+                     float* out);
+
+/* The same two calls with an explicit path (gbmi_path). */
+gbmi_status gbmi_mi_all_pairs_path(const uint8_t* X, int64_t m, int64_t n, float* out, int path);
+gbmi_status gbmi_mi_cross_path(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
+                               int64_t n2, float* out, int path);
+
+/* Host-buffer variants: X, Y and out are HOST pointers (pinned or pageable).
+ * The call copies the inputs to the device, computes on the current stream,
+ * copies the result back and returns only when out is filled. */
+gbmi_status mi_all_pairs_host(const uint8_t* X, int64_t m, int64_t n, float* out);
+gbmi_status mi_cross_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
+                          float* out);
+
+/* ------------------------------------------------------ counts and pieces */
+
+/* Co-occurrence counts N11 = X^T X (G11 of Sec. 2 step 2) as int32, n x n,
+ * both triangles written.  path = GBMI_PATH_PLAIN (tensor cores, FP8 operands,
+ * FP32 accumulation in exact chunks) or GBMI_PATH_POPCOUNT (bit-packed AND +
+ * popcount).  Both must agree bit for bit. */
+gbmi_status gbmi_counts_all_pairs(const uint8_t* X, int64_t m, int64_t n, int32_t* n11, int path);
+
+/* N11 = X^T Y, n1 x n2 int32, with the same path choice. */
+gbmi_status gbmi_counts_cross(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
+                              int64_t n2, int32_t* n11, int path);
+
+/* Column counts v_j = number of ones in column j (Sec. 3.1, Term 2: v = D^T 1),
+ * int32, length n. */
+gbmi_status gbmi_column_counts(const uint8_t* X, int64_t m, int64_t n, int32_t* v);
+
+/* Elementwise MI from counts (the second half of the plain path): for every
+ * (i, j), n11 = N11[i*n2 + j], derive N10, N01, N00 by Eq. 6-7 from va[i],
+ * vb[j] and m, and write MI in bits to out[i*n2 + j].  All pointers device. */
+gbmi_status gbmi_mi_from_counts(const int32_t* N11, const int32_t* va, const int32_t* vb,
+                                int64_t m, int64_t n1, int64_t n2, float* out);
+
+/* Check that every entry of X is 0 or 1.  Synchronous; returns GBMI_OK or
+ * GBMI_ERR_NOT_BINARY. */
+gbmi_status gbmi_validate_binary(const uint8_t* X, int64_t m, int64_t n);
+
+/* ------------------------------------------------------------ management */
+
+/* Set the CUDA stream (a cudaStream_t, NULL = legacy default stream) used by
+ * all subsequent calls from any host thread. */
+gbmi_status gbmi_set_stream(void* stream);
+void* gbmi_get_stream(void);
+
+/* Set an option (gbmi_option) for subsequent calls. */
+gbmi_status gbmi_set_option(int option, int64_t value);
+
+/* Wait for the current stream, then report and clear the device error word:
+ * GBMI_ERR_TIMEOUT if a bounded wait in a kernel gave up, GBMI_ERR_CUDA on an
+ * asynchronous CUDA error, else GBMI_OK. */
+gbmi_status gbmi_sync(void);
+
+/* Human-readable text of the last error on this host thread ("" if none). */
+const char* gbmi_last_error_string(void);
+
+/* Number of kernels this library has launched since load (a monotone count). */
+uint64_t gbmi_launch_count(void);
+
+/* Free the workspace (waits for the device first). */
+gbmi_status gbmi_shutdown(void);
+
+/* Per-kernel launch profile (enable with GBMI_OPT_PROFILE).  Each kernel
+ * launch is bracketed by CUDA events on the library's stream;
+ * gbmi_profile_entries() waits for the recorded launches, folds them into
+ * per-kernel totals and returns the number of kernel names k; entry k has a
+ * name, a total device time in ms and a launch count.  gbmi_profile_reset()
+ * clears the totals.  The returned name stays valid until the next reset. */
+int gbmi_profile_entries(void);
+const char* gbmi_profile_name(int k);
+double gbmi_profile_ms(int k);
+int64_t gbmi_profile_launches(int k);
+gbmi_status gbmi_profile_reset(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int gbmi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBMI_H_ */

@@ -1,0 +1,384 @@
+// Co-occurrence Gram N11 = X^T X (G11, Sec. 2 step 2) on the tcgen05 tensor
+// cores, with the count derivation of Eq. 6-7 and the MI of Eq. 1/Eq. 2
+// fused into the epilogue (the paper's "only one matrix multiplication",
+// Sec. 3.1, with everything after it done per tile while it is on chip).
+//
+// Operands: the packed matrix P (one row per variable, FP8 E4M3 0x00/0x38 per
+// sample).  0 and 1 are exact in E4M3, every product is 0 or 1 and the FP32
+// accumulator holds integers exactly below 2^24, so a tile's counts are exact
+// as long as one launch accumulates at most 2^24 samples (k_blocks * 128).
+//
+// Persistent, warp-specialised CTA (192 threads, one CTA per SM):
+//   warp 0      TMA producer: 128 x 128-byte slice of A (variables of tile
+//               row I) and 256 x 128-byte slice of B (tile column J) per
+//               stage into a 4-stage shared-memory ring (128-byte swizzle).
+//   warp 1      allocates 512 TMEM columns; one thread issues
+//               tcgen05.mma.kind::f8f6f4 M=128 N=256 K=32 (4 per stage) into
+//               one of two 256-column FP32 accumulators, commits each stage
+//               back to the ring and each finished tile to the epilogue.
+//   warps 2-5   epilogue: tcgen05.ld the accumulator (one TMEM lane = one
+//               variable i per thread), derive n10, n01, n00, evaluate MI and
+//               store (i, j) and, for a symmetric problem, (j, i).  The
+//               second accumulator lets tile t+1's MMAs run meanwhile.
+// Tiles come from a host-built list: for all-pairs only blocks that touch
+// the upper triangle (j >= i), in groups of column blocks so that CTAs running
+// at the same time share operand panels in L2.
+//
+// Every mbarrier wait is bounded (timeout_ns from its start, %globaltimer).  A role whose
+// wait runs out sets a bit in the device error word and a CTA-wide abort flag;
+// the other roles see the flag and unwind; the producer waits (bounded) for
+// its copies still in flight, the MMA thread for its MMAs, and warp 1 frees
+// the tensor memory before the CTA exits.
+#include "internal.cuh"
+#include "ptx.cuh"
+
+namespace gbmi {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kThreads = 192;
+constexpr int kUmmaK = 32;                       // K per MMA for 8-bit inputs
+constexpr int kABytes = kTcBM * kTcBK;           // 16 KB
+constexpr int kBBytes = kTcBN * kTcBK;           // 32 KB
+constexpr int kStageBytes = kABytes + kBBytes;   // 48 KB
+constexpr int kAccCols = kTcBN;                  // FP32 columns per accumulator
+constexpr int kTmemCols = 2 * kAccCols;          // 512: the whole tensor memory
+constexpr int kStageWords = 32 * 33;             // epilogue staging per warp (padded)
+constexpr int kEpiWarps = 4;
+
+constexpr size_t kOffStages = 0;
+constexpr size_t kOffStaging = kOffStages + static_cast<size_t>(kStages) * kStageBytes;
+constexpr size_t kOffBars = kOffStaging + static_cast<size_t>(kEpiWarps) * kStageWords * 4;
+constexpr int kNumBars = 2 * kStages + 4 + 1;    // full, empty, tmem full x2, tmem empty x2, drain
+constexpr size_t kOffMisc = kOffBars + kNumBars * 8;
+constexpr size_t kSmemBytes = 1024 + kOffMisc + 64;
+
+static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte alignment");
+static_assert(kOffBars % 8 == 0, "barriers need 8-byte alignment");
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+struct Smem {
+    uint8_t* base;
+    __device__ uint8_t* a(int s) const { return base + kOffStages + s * kStageBytes; }
+    __device__ uint8_t* b(int s) const { return base + kOffStages + s * kStageBytes + kABytes; }
+    __device__ uint32_t* staging(int w) const {
+        return reinterpret_cast<uint32_t*>(base + kOffStaging) + w * kStageWords;
+    }
+    __device__ uint64_t* bar(int k) const { return reinterpret_cast<uint64_t*>(base + kOffBars) + k; }
+    __device__ uint32_t full(int s) const { return ptx::smem_u32(bar(s)); }
+    __device__ uint32_t empty(int s) const { return ptx::smem_u32(bar(kStages + s)); }
+    __device__ uint32_t tfull(int b) const { return ptx::smem_u32(bar(2 * kStages + b)); }
+    __device__ uint32_t tempty(int b) const { return ptx::smem_u32(bar(2 * kStages + 2 + b)); }
+    __device__ uint32_t drain() const { return ptx::smem_u32(bar(2 * kStages + 4)); }
+    __device__ uint32_t* tmem_holder() const {
+        return reinterpret_cast<uint32_t*>(base + kOffMisc);
+    }
+    __device__ volatile int* abort_flag() const {
+        return reinterpret_cast<volatile int*>(base + kOffMisc + 4);
+    }
+};
+
+__device__ __forceinline__ void raise_abort(const Smem& sm, unsigned int* err, uint32_t code) {
+    atomicOr(err, code);
+    *sm.abort_flag() = 1;
+}
+
+// ------------------------------------------------------------------ producer
+__device__ void run_producer(const Smem& sm, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                             const TcArgs& a) {
+    int pending_parity[kStages];
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) pending_parity[s] = -1;
+    if (a.debug_flags & 1) return;   // test hook: issue nothing, consumers must time out
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
+        const int2 tile = a.tiles[t];
+        const int yA = tile.x * kTcBM;
+        const int yB = tile.y * kTcBN;
+        for (int kb = 0; kb < a.k_blocks; ++kb) {
+            if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, a.timeout_ns, sm.abort_flag())) {
+                raise_abort(sm, a.err, kErrTimeoutLoad);
+                ok = false;
+                break;
+            }
+            ptx::mbar_arrive_expect_tx(sm.full(stage), kStageBytes);
+            const int x = (a.k_begin + kb) * kTcBK;
+            ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), tmA, sm.full(stage), x, yA);
+            ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), tmB, sm.full(stage), x, yB);
+            pending_parity[stage] = static_cast<int>(phase);
+            if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1u;
+            }
+        }
+    }
+    if (!ok || *sm.abort_flag()) {
+        // Unwinding: wait (bounded) until every copy this thread issued has landed.
+        const uint64_t d2 = ptx::globaltimer_ns() + 100000000ull;
+        for (int s = 0; s < kStages; ++s) {
+            if (pending_parity[s] < 0) continue;
+            const uint32_t bar = sm.full(s);
+            const uint32_t par = static_cast<uint32_t>(pending_parity[s]);
+            while (!ptx::mbar_try_wait(bar, par)) {
+                if (ptx::globaltimer_ns() > d2) {
+                    atomicOr(a.err, kErrTimeoutDrain);
+                    break;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ MMA issuer
+__device__ void run_mma(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
+    const uint32_t idesc = ptx::idesc_e4m3_f32(kTcBM, kTcBN);
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
+        if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, a.timeout_ns, sm.abort_flag())) {
+            raise_abort(sm, a.err, kErrTimeoutMma);
+            break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kAccCols);
+        for (int kb = 0; kb < a.k_blocks; ++kb) {
+            if (!ptx::mbar_wait_bounded(sm.full(stage), phase, a.timeout_ns, sm.abort_flag())) {
+                raise_abort(sm, a.err, kErrTimeoutMma);
+                ok = false;
+                break;
+            }
+            ptx::tc_fence_after();
+            const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
+            const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
+#pragma unroll
+            for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                // advance the start address by kk * 32 bytes inside the swizzle row
+                const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+                ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
+                                (kb | kk) != 0 ? 1u : 0u);
+            }
+            ptx::mma_commit(sm.empty(stage));   // frees the slot when these MMAs finish
+            if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1u;
+            }
+        }
+        if (!ok) break;
+        ptx::mma_commit(sm.tfull(acc));         // accumulator ready for the epilogue
+        if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1u;
+        }
+    }
+    // Wait (bounded) for every MMA issued by this thread before TMEM is freed.
+    ptx::mma_commit(sm.drain());
+    const uint64_t d2 = ptx::globaltimer_ns() + 100000000ull;
+    while (!ptx::mbar_try_wait(sm.drain(), 0)) {
+        if (ptx::globaltimer_ns() > d2) {
+            atomicOr(a.err, kErrTimeoutDrain);
+            break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ epilogue
+template <int kMode>
+__device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int lane_base = (warp & 3) * 32;   // TMEM lanes this warp may access
+    uint32_t* stg = sm.staging(warp - 2);
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
+        const int2 tile = a.tiles[t];
+        const int64_t ibase = static_cast<int64_t>(tile.x) * kTcBM + lane_base;
+        const int64_t i = ibase + lane;
+        const int64_t jb = static_cast<int64_t>(tile.y) * kTcBN;
+        if (!ptx::mbar_wait_bounded(sm.tfull(acc), acc_phase, a.timeout_ns, sm.abort_flag())) {
+            raise_abort(sm, a.err, kErrTimeoutEpilogue);
+            break;
+        }
+        ptx::tc_fence_after();
+        const bool row_ok = i < a.n_a;
+        int64_t vi = 0;
+        double hi = 0.0;
+        if (kMode == kTcModeMI && row_ok) {
+            vi = a.va[i];
+            if (a.ha) hi = a.ha[i];
+        }
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(lane_base) << 16) +
+                               static_cast<uint32_t>(acc * kAccCols);
+#pragma unroll 1
+        for (int c = 0; c < kTcBN; c += 32) {
+            const int64_t j0 = jb + c;
+            // warp-uniform skips: chunk beyond the last variable, or (symmetric)
+            // entirely below the diagonal for this warp's 32 rows
+            if (j0 >= a.n_b) break;
+            if (a.symmetric && j0 + 31 < ibase) continue;
+            uint32_t r[32];
+            ptx::tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c), r);
+            ptx::tmem_wait_ld();
+            // park the 32 accumulator columns in this lane's column of the
+            // staging block; each lane only touches its own column until the
+            // __syncwarp below
+#pragma unroll
+            for (int q = 0; q < 32; ++q) stg[q * 33 + lane] = r[q];
+#pragma unroll 2
+            for (int q = 0; q < 32; ++q) {
+                const int64_t j = j0 + q;
+                const int32_t n11 = __float2int_rn(__uint_as_float(stg[q * 33 + lane]));
+                uint32_t val;
+                if (kMode == kTcModeMI) {
+                    float mi = 0.f;
+                    if (row_ok && j < a.n_b && (!a.symmetric || j >= i)) {
+                        const double hj = a.hb ? a.hb[j] : 0.0;
+                        mi = mi_pair(n11, vi, a.vb[j], hi, hj, a.mp);
+                    }
+                    val = __float_as_uint(mi);
+                } else {
+                    val = static_cast<uint32_t>(n11);
+                }
+                stg[q * 33 + lane] = val;
+                // (j, i): lanes hold consecutive i -> coalesced rows of the output
+                if (a.symmetric && row_ok && j < a.n_b && j > i) {
+                    if (kMode == kTcModeMI) {
+                        a.out_f[j * a.ld_out + i] = __uint_as_float(val);
+                    } else if (kMode == kTcModeCounts) {
+                        a.out_c[j * a.ld_out + i] = static_cast<int32_t>(val);
+                    } else {
+                        a.out_c[j * a.ld_out + i] += static_cast<int32_t>(val);
+                    }
+                }
+            }
+            // (i, j): read the 32 x 32 block transposed so that each store
+            // instruction writes one contiguous row segment
+            __syncwarp();
+            const int64_t jj = j0 + lane;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const int64_t ii = ibase + rr;
+                if (ii < a.n_a && jj < a.n_b && (!a.symmetric || jj >= ii)) {
+                    const uint32_t x = stg[lane * 33 + rr];
+                    if (kMode == kTcModeMI) {
+                        a.out_f[ii * a.ld_out + jj] = __uint_as_float(x);
+                    } else if (kMode == kTcModeCounts) {
+                        a.out_c[ii * a.ld_out + jj] = static_cast<int32_t>(x);
+                    } else {
+                        a.out_c[ii * a.ld_out + jj] += static_cast<int32_t>(x);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(sm.tempty(acc));
+        if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1u;
+        }
+    }
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kThreads, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    Smem sm;
+    sm.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                         ~static_cast<uintptr_t>(1023));
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            ptx::mbar_init(sm.full(s), 1);
+            ptx::mbar_init(sm.empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(sm.tfull(b), 1);
+            ptx::mbar_init(sm.tempty(b), kEpiWarps * 32);
+        }
+        ptx::mbar_init(sm.drain(), 1);
+        *sm.abort_flag() = 0;
+        ptx::fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        ptx::tma_prefetch_desc(&tmA);
+        ptx::tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(ptx::smem_u32(sm.tmem_holder()), kTmemCols);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *sm.tmem_holder();
+
+    if (warp == 0) {
+        if (lane == 0) run_producer(sm, &tmA, &tmB, a);
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) run_mma(sm, a, tmem_base);
+        __syncwarp();
+    } else {
+        run_epilogue<kMode>(sm, a, tmem_base);
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+}  // namespace
+
+size_t gram_tc_smem_bytes() { return kSmemBytes; }
+
+cudaError_t gram_tc_prepare() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeCounts>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(gram_tc_kernel<kTcModeCountsAdd>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kSmemBytes));
+}
+
+cudaError_t launch_gram_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a,
+                           int grid, cudaStream_t s) {
+    if (a.num_tiles <= 0 || grid <= 0) return cudaSuccess;
+    if (a.k_blocks <= 0 || static_cast<int64_t>(a.k_blocks) * kTcBK > (int64_t{1} << 24))
+        return cudaErrorInvalidValue;
+    switch (a.mode) {
+        case kTcModeMI:
+            gram_tc_kernel<kTcModeMI><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, a);
+            break;
+        case kTcModeCounts:
+            gram_tc_kernel<kTcModeCounts><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, a);
+            break;
+        case kTcModeCountsAdd:
+            gram_tc_kernel<kTcModeCountsAdd><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gbmi

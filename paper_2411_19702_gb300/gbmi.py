@@ -1,0 +1,297 @@
+"""Python binding of libgbmi.so (ctypes): argument marshalling only.
+
+Every function takes torch CUDA tensors (or numpy arrays for the ``*_host``
+calls), checks dtypes and shapes, points the library at the tensor's current
+stream and calls the C ABI of ``include/gbmi.h`` with raw pointers.  All
+computation happens in the library's CUDA kernels.  There is no fallback: if
+the library is missing or the GPU is not sm_103a, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgbmi.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gbmi.h")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_BINARY, ERR_UNSUPPORTED = range(7)
+PATH_AUTO, PATH_FUSED, PATH_PLAIN, PATH_POPCOUNT = range(4)
+OPT_FIXUP, OPT_TIMEOUT_NS, OPT_DEBUG_FLAGS, OPT_GROUP_COLS, OPT_MAX_CTAS, OPT_PROFILE = range(1, 7)
+_PATHS = {"auto": PATH_AUTO, "fused": PATH_FUSED, "plain": PATH_PLAIN, "popcount": PATH_POPCOUNT}
+STATUS_NAMES = {OK: "OK", ERR_ARG: "ERR_ARG", ERR_OOM: "ERR_OOM", ERR_CUDA: "ERR_CUDA",
+                ERR_TIMEOUT: "ERR_TIMEOUT", ERR_NOT_BINARY: "ERR_NOT_BINARY",
+                ERR_UNSUPPORTED: "ERR_UNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GbmiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/gbmi.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return re.findall(
+        r"^\s*(?:gbmi_status|void\*|const char\*|uint64_t|int64_t|double|int)\s+(\w+)\s*\(",
+        text, flags=re.M)
+
+
+def load(path: str | None = None):
+    """Load libgbmi.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libgbmi.so not found at {p}: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        sig = {
+            "mi_all_pairs": [vp, i64, i64, vp],
+            "mi_cross": [vp, vp, i64, i64, i64, vp],
+            "gbmi_mi_all_pairs_path": [vp, i64, i64, vp, i32],
+            "gbmi_mi_cross_path": [vp, vp, i64, i64, i64, vp, i32],
+            "mi_all_pairs_host": [vp, i64, i64, vp],
+            "mi_cross_host": [vp, vp, i64, i64, i64, vp],
+            "gbmi_counts_all_pairs": [vp, i64, i64, vp, i32],
+            "gbmi_counts_cross": [vp, vp, i64, i64, i64, vp, i32],
+            "gbmi_column_counts": [vp, i64, i64, vp],
+            "gbmi_mi_from_counts": [vp, vp, vp, i64, i64, i64, vp],
+            "gbmi_validate_binary": [vp, i64, i64],
+            "gbmi_set_stream": [vp],
+            "gbmi_set_option": [i32, i64],
+            "gbmi_sync": [],
+            "gbmi_shutdown": [],
+            "gbmi_profile_reset": [],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.gbmi_get_stream.argtypes = []
+        lib.gbmi_get_stream.restype = ctypes.c_void_p
+        lib.gbmi_last_error_string.argtypes = []
+        lib.gbmi_last_error_string.restype = ctypes.c_char_p
+        lib.gbmi_launch_count.argtypes = []
+        lib.gbmi_launch_count.restype = ctypes.c_uint64
+        lib.gbmi_version.argtypes = []
+        lib.gbmi_version.restype = ctypes.c_int
+        lib.gbmi_profile_entries.argtypes = []
+        lib.gbmi_profile_entries.restype = ctypes.c_int
+        lib.gbmi_profile_name.argtypes = [ctypes.c_int]
+        lib.gbmi_profile_name.restype = ctypes.c_char_p
+        lib.gbmi_profile_ms.argtypes = [ctypes.c_int]
+        lib.gbmi_profile_ms.restype = ctypes.c_double
+        lib.gbmi_profile_launches.argtypes = [ctypes.c_int]
+        lib.gbmi_profile_launches.restype = ctypes.c_int64
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != OK:
+        msg = load().gbmi_last_error_string()
+        raise GbmiError(status, msg.decode() if msg else "")
+
+
+def _path(path) -> int:
+    return _PATHS[path] if isinstance(path, str) else int(path)
+
+
+def _prep(X, name="X"):
+    import torch
+    if not isinstance(X, torch.Tensor) or not X.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if X.dtype not in (torch.uint8, torch.bool):
+        raise TypeError(f"{name} must be uint8 (0/1) or bool")
+    if X.dim() != 2:
+        raise ValueError(f"{name} must be 2-D (samples x variables)")
+    if X.dtype == torch.bool:
+        X = X.view(torch.uint8)
+    return X.contiguous()
+
+
+def _bind_stream(dev):
+    import torch
+    lib = load()
+    _check(lib.gbmi_set_stream(ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
+    return lib
+
+
+def mi_all_pairs(X, out=None, path="auto"):
+    """n x n MI matrix (bits, float32) of the columns of X (m x n, uint8 0/1)."""
+    import torch
+    X = _prep(X)
+    m, n = X.shape
+    with torch.cuda.device(X.device):
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float32, device=X.device)
+        assert out.shape == (n, n) and out.dtype == torch.float32 and out.is_contiguous()
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_mi_all_pairs_path(X.data_ptr(), m, n, out.data_ptr(), _path(path)))
+    return out
+
+
+def mi_cross(X, Y, out=None, path="auto"):
+    """n1 x n2 MI matrix between the columns of X (m x n1) and Y (m x n2)."""
+    import torch
+    X, Y = _prep(X), _prep(Y, "Y")
+    if X.shape[0] != Y.shape[0]:
+        raise ValueError("X and Y must have the same number of samples")
+    m, n1 = X.shape
+    n2 = Y.shape[1]
+    with torch.cuda.device(X.device):
+        if out is None:
+            out = torch.empty((n1, n2), dtype=torch.float32, device=X.device)
+        assert out.shape == (n1, n2) and out.dtype == torch.float32 and out.is_contiguous()
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_mi_cross_path(X.data_ptr(), Y.data_ptr(), m, n1, n2, out.data_ptr(),
+                                      _path(path)))
+    return out
+
+
+def counts_all_pairs(X, path="plain", out=None):
+    """N11 = X^T X as int32 (n x n) via the tensor cores ("plain") or popcount."""
+    import torch
+    X = _prep(X)
+    m, n = X.shape
+    with torch.cuda.device(X.device):
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.int32, device=X.device)
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_counts_all_pairs(X.data_ptr(), m, n, out.data_ptr(), _path(path)))
+    return out
+
+
+def counts_cross(X, Y, path="plain", out=None):
+    """N11 = X^T Y as int32 (n1 x n2)."""
+    import torch
+    X, Y = _prep(X), _prep(Y, "Y")
+    m, n1 = X.shape
+    n2 = Y.shape[1]
+    with torch.cuda.device(X.device):
+        if out is None:
+            out = torch.empty((n1, n2), dtype=torch.int32, device=X.device)
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_counts_cross(X.data_ptr(), Y.data_ptr(), m, n1, n2, out.data_ptr(),
+                                     _path(path)))
+    return out
+
+
+def column_counts(X):
+    """v_j = number of ones in column j (int32)."""
+    import torch
+    X = _prep(X)
+    m, n = X.shape
+    with torch.cuda.device(X.device):
+        v = torch.empty(n, dtype=torch.int32, device=X.device)
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_column_counts(X.data_ptr(), m, n, v.data_ptr()))
+    return v
+
+
+def mi_from_counts(N11, va, vb, m, out=None):
+    """Elementwise MI (bits) from an int32 count matrix and the column counts."""
+    import torch
+    n1, n2 = N11.shape
+    N11, va, vb = N11.contiguous(), va.contiguous(), vb.contiguous()
+    with torch.cuda.device(N11.device):
+        if out is None:
+            out = torch.empty((n1, n2), dtype=torch.float32, device=N11.device)
+        lib = _bind_stream(N11.device)
+        _check(lib.gbmi_mi_from_counts(N11.data_ptr(), va.data_ptr(), vb.data_ptr(), int(m), n1,
+                                       n2, out.data_ptr()))
+    return out
+
+
+def validate_binary(X) -> bool:
+    """True if every entry of X is 0 or 1 (synchronous)."""
+    import torch
+    X = _prep(X)
+    with torch.cuda.device(X.device):
+        lib = _bind_stream(X.device)
+        st = lib.gbmi_validate_binary(X.data_ptr(), X.shape[0], X.shape[1])
+    if st == ERR_NOT_BINARY:
+        return False
+    _check(st)
+    return True
+
+
+def mi_all_pairs_host(X, out=None):
+    """Host-buffer call: X is a numpy/torch CPU uint8 array; returns a CPU float32 array."""
+    import numpy as np
+    Xn = np.ascontiguousarray(X, dtype=np.uint8) if not hasattr(X, "data_ptr") else X
+    m, n = Xn.shape
+    if out is None:
+        out = np.empty((n, n), dtype=np.float32)
+    xp = Xn.data_ptr() if hasattr(Xn, "data_ptr") else Xn.ctypes.data
+    op = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    lib = load()
+    _check(lib.mi_all_pairs_host(xp, m, n, op))
+    return out
+
+
+def mi_cross_host(X, Y, out=None):
+    import numpy as np
+    Xn = np.ascontiguousarray(X, dtype=np.uint8)
+    Yn = np.ascontiguousarray(Y, dtype=np.uint8)
+    m, n1 = Xn.shape
+    n2 = Yn.shape[1]
+    if out is None:
+        out = np.empty((n1, n2), dtype=np.float32)
+    _check(load().mi_cross_host(Xn.ctypes.data, Yn.ctypes.data, m, n1, n2, out.ctypes.data))
+    return out
+
+
+def set_option(option: int, value: int):
+    _check(load().gbmi_set_option(int(option), int(value)))
+
+
+def sync():
+    """Wait for the library's stream and raise on a device-side timeout."""
+    _check(load().gbmi_sync())
+
+
+def launch_count() -> int:
+    return int(load().gbmi_launch_count())
+
+
+def last_error() -> str:
+    s = load().gbmi_last_error_string()
+    return s.decode() if s else ""
+
+
+def shutdown():
+    _check(load().gbmi_shutdown())
+
+
+def version() -> int:
+    return int(load().gbmi_version())
+
+
+def profile(enable: bool | None = None, reset: bool = False) -> dict:
+    """Per-kernel device time from the library's event profiler.
+
+    enable=True/False switches recording on/off; the return value maps each
+    kernel name to {"ms": total ms, "launches": count} (waits for the work).
+    """
+    lib = load()
+    if reset:
+        _check(lib.gbmi_profile_reset())
+    if enable is not None:
+        set_option(OPT_PROFILE, 1 if enable else 0)
+    out = {}
+    for k in range(lib.gbmi_profile_entries()):
+        out[lib.gbmi_profile_name(k).decode()] = {"ms": float(lib.gbmi_profile_ms(k)),
+                                                  "launches": int(lib.gbmi_profile_launches(k))}
+    return out

@@ -1,0 +1,99 @@
+"""Exact counts at the accumulation limits, and the bounded device-side waits.
+
+FP32 accumulation of 0/1 FP8 products is exact while a count stays at most
+2^24; one Gram launch therefore accumulates at most 2^24 samples and the
+plain path adds launch results in int32.  All-ones columns make every
+accumulator reach m, the largest value it can hold for that m.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2411_19702_gb300 import gbmi  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _reset_options():
+    gbmi.set_option(gbmi.OPT_DEBUG_FLAGS, 0)
+    gbmi.set_option(gbmi.OPT_TIMEOUT_NS, 2_000_000_000)
+    yield
+    gbmi.set_option(gbmi.OPT_DEBUG_FLAGS, 0)
+    gbmi.set_option(gbmi.OPT_TIMEOUT_NS, 2_000_000_000)
+
+
+@pytest.mark.parametrize("m", [1 << 10, 1 << 14, (1 << 20) + 3, 1 << 24])
+def test_all_ones_counts_reach_m(m):
+    n = 8
+    X = torch.ones((m, n), dtype=torch.uint8, device="cuda")
+    for path in ("plain", "popcount"):
+        c = gbmi.counts_all_pairs(X, path=path)
+        gbmi.sync()
+        assert torch.all(c == m).item(), f"{path}: counts differ from m={m}"
+    # fused MI: constant columns carry no information
+    if m <= (1 << 24):
+        out = gbmi.mi_all_pairs(X, path="fused")
+        gbmi.sync()
+        assert torch.all(out == 0).item()
+
+
+def test_counts_beyond_one_exact_chunk():
+    """m = 2^24 + 129: two Gram launches whose int32 results are added."""
+    m, n = (1 << 24) + 129, 8
+    X = torch.ones((m, n), dtype=torch.uint8, device="cuda")
+    X[5:, 3] = 0          # column 3 has 5 ones
+    X[::2, 4] = 0         # column 4 has ceil(m/2) ones at odd rows
+    c = gbmi.counts_all_pairs(X, path="plain")
+    p = gbmi.counts_all_pairs(X, path="popcount")
+    gbmi.sync()
+    assert torch.equal(c, p)
+    assert c[0, 0].item() == m and c[3, 3].item() == 5 and c[4, 4].item() == m // 2
+    # AUTO falls back to the plain path beyond 2^24 samples; MI of the
+    # constant columns is 0 and MI(col 3; col 4) matches the oracle's counts
+    out = gbmi.mi_all_pairs(X, path="auto")
+    gbmi.sync()
+    cnt = c.cpu().numpy().astype(np.int64)
+    n11 = cnt[3, 4]
+    v3, v4 = cnt[3, 3], cnt[4, 4]
+    want = oracle.mi_from_counts(n11, v3 - n11, v4 - n11, m - v3 - v4 + n11)
+    assert abs(float(out[3, 4]) - want) <= 1e-6
+    assert float(out[0, 1]) == 0.0
+
+
+def test_random_counts_at_precision_m_match_popcount():
+    m, n = 1 << 20, 384
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    p = torch.rand(n, generator=g, device="cuda") * 0.48 + 0.02
+    X = (torch.rand((m, n), generator=g, device="cuda") < p).to(torch.uint8)
+    a = gbmi.counts_all_pairs(X, path="plain")
+    b = gbmi.counts_all_pairs(X, path="popcount")
+    gbmi.sync()
+    assert torch.equal(a, b)
+    assert torch.equal(torch.diagonal(a), X.sum(dim=0, dtype=torch.int32))
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """The fused kernel's loader issues no copies (test hook), so its MMA
+    thread's wait on the first stage can never complete: it must give up after
+    the timeout, report GBMI_ERR_TIMEOUT, free its tensor memory and leave the
+    context usable."""
+    X = torch.from_numpy((np.random.default_rng(1).random((512, 300)) < 0.3)
+                         .astype(np.uint8)).cuda()
+    gbmi.set_option(gbmi.OPT_TIMEOUT_NS, 50_000_000)
+    gbmi.set_option(gbmi.OPT_DEBUG_FLAGS, 1)
+    gbmi.mi_all_pairs(X, path="fused")
+    with pytest.raises(gbmi.GbmiError) as e:
+        gbmi.sync()
+    assert e.value.status == gbmi.ERR_TIMEOUT
+    gbmi.set_option(gbmi.OPT_DEBUG_FLAGS, 0)
+    gbmi.set_option(gbmi.OPT_TIMEOUT_NS, 2_000_000_000)
+    out = gbmi.mi_all_pairs(X, path="fused")
+    gbmi.sync()
+    want, _ = oracle.mi_matrix(X.cpu().numpy())
+    assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - want)) <= 1e-6
