@@ -61,7 +61,7 @@ typedef enum {
 
 /* Options for gbmi_set_option. */
 typedef enum {
-    GBMI_OPT_FIXUP = 1,          /* 1 (default): FP64 n*log2(n) combine for pairs whose FP32 MI < 1e-4 */
+    GBMI_OPT_FIXUP = 1,          /* 1: FP64 n*log2(n) combine for pairs whose FP32 MI < 1e-4 (default 0) */
     GBMI_OPT_TIMEOUT_NS = 2,     /* bound of every device-side wait, ns (default 2e9)            */
     GBMI_OPT_DEBUG_FLAGS = 3,    /* test hooks; 1 = the fused kernel's loader issues no copies,
                                     so its consumer's bounded wait must run out (default 0)      */

@@ -33,7 +33,7 @@ std::atomic<uint64_t> g_launches{0};
 cudaStream_t g_stream = nullptr;
 
 struct Options {
-    int fixup = 1;
+    int fixup = 0;   // FP64 combine off: the FP32 h-form has no cancellation (see mi_device.cuh)
     uint64_t timeout_ns = 2000000000ull;
     int debug_flags = 0;
     int group_cols = 8;
@@ -48,7 +48,7 @@ struct DevBuf {
 struct DeviceCtx {
     bool ready = false;
     int sm_count = 0;
-    DevBuf Pa, Pb, Ba, Bb, va, vb, ha, hb, counts, T, err, tiles, Xs, Ys, outs, flag;
+    DevBuf Pa, Pb, Ba, Bb, va, vb, ha, hb, counts, T, err, tiles, Xs, Ys, outs, flag;  // ha/hb: MiVar
     int64_t T_len = 0;
     // tile-list cache
     int64_t tl_na = -1, tl_nb = -1;
@@ -251,12 +251,15 @@ gbmi_status pack(DeviceCtx& c, const uint8_t* X, int64_t m, int64_t n, DevBuf* P
 }
 
 gbmi_status mi_params(DeviceCtx& c, int64_t m, MiParams* P) {
-    P->m = m;
+    P->m = static_cast<int32_t>(m);
     P->fm = static_cast<float>(m);
     P->inv_m_ln2 = static_cast<float>(1.0 / (static_cast<double>(m) * std::log(2.0)));
-    P->inv_m = 1.0 / static_cast<double>(m);
+    P->inv_m = static_cast<float>(1.0 / static_cast<double>(m));
     P->fixup = g_opt.fixup ? 1 : 0;
     P->fixup_below = 1e-4f;
+    // chi^2-divergence bound under which MI (bits) is surely below 1e-4; the
+    // factor keeps FP32 rounding of the bound on the safe side
+    P->chi_below = static_cast<float>(1e-4 * std::log(2.0) * (1.0 - 1e-4));
     P->T = nullptr;
     if (P->fixup && m <= kMaxTableM) {
         if (c.T_len < m + 1) {
@@ -272,15 +275,12 @@ gbmi_status mi_params(DeviceCtx& c, int64_t m, MiParams* P) {
     return GBMI_OK;
 }
 
-gbmi_status col_h(DeviceCtx& c, const DevBuf& v, int64_t n, const MiParams& P, DevBuf& h,
-                  const double** out) {
-    *out = nullptr;
-    if (!P.fixup) return GBMI_OK;
-    GBMI_TRY(ensure(h, static_cast<size_t>(n) * 8, "column entropy terms"));
-    GBMI_LAUNCH(launch_col_h(static_cast<const int32_t*>(v.p), n, P, static_cast<double*>(h.p),
-                             g_stream),
-                "col_h");
-    *out = static_cast<const double*>(h.p);
+// Per-variable epilogue terms (MiVar) from the column counts v.
+gbmi_status mi_vars(const int32_t* v, int64_t n, const MiParams& P, DevBuf& out,
+                    const MiVar** res) {
+    GBMI_TRY(ensure(out, static_cast<size_t>(n) * sizeof(MiVar), "per-variable terms"));
+    GBMI_LAUNCH(launch_mi_vars(v, n, P, static_cast<MiVar*>(out.p), g_stream), "mi_vars");
+    *res = static_cast<const MiVar*>(out.p);
     return GBMI_OK;
 }
 
@@ -337,9 +337,8 @@ int grid_for(const DeviceCtx& c, int tiles) {
 // Run the tensor-core Gram over [0, m) in exact chunks.  mode MI needs one
 // chunk (m <= 2^24); the counts modes add chunk results into out_c.
 gbmi_status run_gram(DeviceCtx& c, const DevBuf& Pa, const DevBuf& Pb, int64_t m, int64_t n_a,
-                     int64_t n_b, bool sym, int mode, const int32_t* va, const int32_t* vb,
-                     const double* ha, const double* hb, const MiParams& mp, float* out_f,
-                     int32_t* out_c, int64_t ld_out) {
+                     int64_t n_b, bool sym, int mode, const MiVar* va, const MiVar* vb,
+                     const MiParams& mp, float* out_f, int32_t* out_c, int64_t ld_out) {
     const int64_t ldp = pack_ld(m);
     const int64_t rows_a = pack_rows(n_a), rows_b = pack_rows(n_b);
     CUtensorMap tmA, tmB;
@@ -356,12 +355,13 @@ gbmi_status run_gram(DeviceCtx& c, const DevBuf& Pa, const DevBuf& Pb, int64_t m
     a.symmetric = sym ? 1 : 0;
     a.va = va;
     a.vb = vb;
-    a.ha = ha;
-    a.hb = hb;
     a.mp = mp;
     a.out_f = out_f;
     a.out_c = out_c;
     a.ld_out = ld_out;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(out_f ? static_cast<void*>(out_f)
+                                                             : static_cast<void*>(out_c));
+    a.vec_store = (ld_out % 4 == 0 && base % 16 == 0) ? 1 : 0;
     a.err = static_cast<unsigned int*>(c.err.p);
     a.timeout_ns = g_opt.timeout_ns;
     a.debug_flags = g_opt.debug_flags;
@@ -408,17 +408,14 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
     const bool popc = path == GBMI_PATH_POPCOUNT;
     GBMI_TRY(pack(c, X, m, n1, popc ? nullptr : &c.Pa, popc ? &c.Ba : nullptr, c.va));
     if (!sym) GBMI_TRY(pack(c, Y, m, n2, popc ? nullptr : &c.Pb, popc ? &c.Bb : nullptr, c.vb));
-    DevBuf& vb = sym ? c.va : c.vb;
     MiParams mp;
     GBMI_TRY(mi_params(c, m, &mp));
-    const double *ha = nullptr, *hb = nullptr;
-    GBMI_TRY(col_h(c, c.va, n1, mp, c.ha, &ha));
+    const MiVar *va = nullptr, *vbp = nullptr;
+    GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.va.p), n1, mp, c.ha, &va));
     if (sym)
-        hb = ha;
+        vbp = va;
     else
-        GBMI_TRY(col_h(c, c.vb, n2, mp, c.hb, &hb));
-    const int32_t* va = static_cast<const int32_t*>(c.va.p);
-    const int32_t* vbp = static_cast<const int32_t*>(vb.p);
+        GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.vb.p), n2, mp, c.hb, &vbp));
 
     if (popc) {
         PopcArgs a;
@@ -430,8 +427,6 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
         a.symmetric = sym ? 1 : 0;
         a.va = va;
         a.vb = vbp;
-        a.ha = ha;
-        a.hb = hb;
         a.mp = mp;
         a.out_f = out;
         a.out_c = nullptr;
@@ -441,14 +436,13 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
     }
     const DevBuf& Pb = sym ? c.Pa : c.Pb;
     if (path == GBMI_PATH_FUSED)
-        return run_gram(c, c.Pa, Pb, m, n1, n2, sym, kTcModeMI, va, vbp, ha, hb, mp, out,
-                        nullptr, n2);
+        return run_gram(c, c.Pa, Pb, m, n1, n2, sym, kTcModeMI, va, vbp, mp, out, nullptr, n2);
     // plain: exact counts to HBM, then the elementwise MI kernel
     GBMI_TRY(ensure(c.counts, static_cast<size_t>(n1) * n2 * 4, "count matrix"));
     int32_t* N11 = static_cast<int32_t*>(c.counts.p);
-    GBMI_TRY(run_gram(c, c.Pa, Pb, m, n1, n2, sym, kTcModeCounts, va, vbp, ha, hb, mp, nullptr,
-                      N11, n2));
-    GBMI_LAUNCH(launch_mi_from_counts(N11, n2, va, vbp, ha, hb, n1, n2, mp, out, n2, g_stream),
+    GBMI_TRY(run_gram(c, c.Pa, Pb, m, n1, n2, sym, kTcModeCounts, va, vbp, mp, nullptr, N11,
+                      n2));
+    GBMI_LAUNCH(launch_mi_from_counts(N11, n2, va, vbp, n1, n2, mp, out, n2, g_stream),
                 "mi_from_counts");
     return GBMI_OK;
 }
@@ -490,7 +484,7 @@ gbmi_status counts_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n
         return GBMI_OK;
     }
     return run_gram(c, c.Pa, sym ? c.Pa : c.Pb, m, n1, n2, sym, kTcModeCounts, nullptr, nullptr,
-                    nullptr, nullptr, mp, nullptr, n11, n2);
+                    mp, nullptr, n11, n2);
 }
 
 gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
@@ -622,16 +616,10 @@ gbmi_status gbmi_mi_from_counts(const int32_t* N11, const int32_t* va, const int
     DeviceCtx& c = *cp;
     MiParams mp;
     GBMI_TRY(mi_params(c, m, &mp));
-    const double *ha = nullptr, *hb = nullptr;
-    if (mp.fixup) {
-        GBMI_TRY(ensure(c.ha, static_cast<size_t>(n1) * 8, "column entropy terms"));
-        GBMI_TRY(ensure(c.hb, static_cast<size_t>(n2) * 8, "column entropy terms"));
-        GBMI_LAUNCH(launch_col_h(va, n1, mp, static_cast<double*>(c.ha.p), g_stream), "col_h");
-        GBMI_LAUNCH(launch_col_h(vb, n2, mp, static_cast<double*>(c.hb.p), g_stream), "col_h");
-        ha = static_cast<const double*>(c.ha.p);
-        hb = static_cast<const double*>(c.hb.p);
-    }
-    GBMI_LAUNCH(launch_mi_from_counts(N11, n2, va, vb, ha, hb, n1, n2, mp, out, n2, g_stream),
+    const MiVar *A = nullptr, *B = nullptr;
+    GBMI_TRY(mi_vars(va, n1, mp, c.ha, &A));
+    GBMI_TRY(mi_vars(vb, n2, mp, c.hb, &B));
+    GBMI_LAUNCH(launch_mi_from_counts(N11, n2, A, B, n1, n2, mp, out, n2, g_stream),
                 "mi_from_counts");
     return GBMI_OK;
 }

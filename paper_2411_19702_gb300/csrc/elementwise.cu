@@ -1,6 +1,8 @@
 // Elementwise kernels:
+//   - zero fill,
 //   - the n*log2(n) table T[k] = k log2 k (FP64) behind the FP64 combine,
-//   - per-variable H_j = T[v_j] + T[m - v_j] (the marginal part of m*MI),
+//   - per-variable epilogue terms (MiVar: reciprocals of the marginal counts
+//     and H_j = T[v_j] + T[m - v_j]),
 //   - MI from a stored count matrix (second half of the plain, unfused path:
 //     Eq. 6-7 counts and Eq. 1/Eq. 2 MI for every (i, j) of N11).
 #include "internal.cuh"
@@ -23,25 +25,23 @@ __global__ void nlogn_table_kernel(double* T, int64_t len) {
     }
 }
 
-__global__ void col_h_kernel(const int32_t* v, int64_t n, const MiParams P, double* h) {
+__global__ void mi_vars_kernel(const int32_t* v, int64_t n, const MiParams P, MiVar* out) {
     for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        h[j] = mi_col_h(v[j], P);
+        out[j] = mi_var(v[j], P);
 }
 
-// One thread per output element, 2-D grid over (row block, column block):
-// threadIdx.x runs along j for coalesced reads of N11 and writes of out.
-__global__ void mi_from_counts_kernel(const int32_t* N11, int64_t ld_n11, const int32_t* va,
-                                      const int32_t* vb, const double* ha, const double* hb,
-                                      int64_t n1, int64_t n2, const MiParams P, float* out,
-                                      int64_t ld_out) {
+// One thread per output element; a CTA covers 256 consecutive j of one row
+// block, so N11 reads and MI writes are coalesced and the row terms uniform.
+__global__ void mi_from_counts_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* va,
+                                      const MiVar* vb, int64_t n1, int64_t n2, const MiParams P,
+                                      float* out, int64_t ld_out) {
     const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (j >= n2) return;
-    const int64_t vj = vb[j];
-    const double hj = hb ? hb[j] : 0.0;
+    const MiVar B = load_var(vb + j);
     for (int64_t i = blockIdx.y; i < n1; i += gridDim.y) {
-        const double hi = ha ? ha[i] : 0.0;
-        out[i * ld_out + j] = mi_pair(N11[i * ld_n11 + j], va[i], vj, hi, hj, P);
+        const MiVar A = load_var(va + i);
+        out[i * ld_out + j] = mi_pair(N11[i * ld_n11 + j], A, B, P);
     }
 }
 
@@ -59,24 +59,22 @@ cudaError_t launch_nlogn_table(double* T, int64_t len, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_col_h(const int32_t* v, int64_t n, const MiParams& P, double* h,
-                         cudaStream_t s) {
+cudaError_t launch_mi_vars(const int32_t* v, int64_t n, const MiParams& P, MiVar* out,
+                           cudaStream_t s) {
     const int64_t blocks = (n + 255) / 256;
-    col_h_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(v, n, P,
-                                                                                     h);
+    mi_vars_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(v, n, P,
+                                                                                       out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const int32_t* va,
-                                  const int32_t* vb, const double* ha, const double* hb,
-                                  int64_t n1, int64_t n2, const MiParams& P, float* out,
-                                  int64_t ld_out, cudaStream_t s) {
+cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const MiVar* va,
+                                  const MiVar* vb, int64_t n1, int64_t n2, const MiParams& P,
+                                  float* out, int64_t ld_out, cudaStream_t s) {
     const int64_t bx = (n2 + 255) / 256;
     if (bx > 0x7FFFFFFF) return cudaErrorInvalidValue;
     const int64_t by = n1 < 65535 ? n1 : 65535;
     dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
-    mi_from_counts_kernel<<<grid, 256, 0, s>>>(N11, ld_n11, va, vb, ha, hb, n1, n2, P, out,
-                                               ld_out);
+    mi_from_counts_kernel<<<grid, 256, 0, s>>>(N11, ld_n11, va, vb, n1, n2, P, out, ld_out);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,7 @@
 // accumulator holds integers exactly below 2^24, so a tile's counts are exact
 // as long as one launch accumulates at most 2^24 samples (k_blocks * 128).
 //
-// Persistent, warp-specialised CTA (192 threads, one CTA per SM):
+// Persistent, warp-specialised CTA (320 threads, one CTA per SM):
 //   warp 0      TMA producer: 128 x 128-byte slice of A (variables of tile
 //               row I) and 256 x 128-byte slice of B (tile column J) per
 //               stage into a 4-stage shared-memory ring (128-byte swizzle).
@@ -16,19 +16,22 @@
 //               tcgen05.mma.kind::f8f6f4 M=128 N=256 K=32 (4 per stage) into
 //               one of two 256-column FP32 accumulators, commits each stage
 //               back to the ring and each finished tile to the epilogue.
-//   warps 2-5   epilogue: tcgen05.ld the accumulator (one TMEM lane = one
-//               variable i per thread), derive n10, n01, n00, evaluate MI and
-//               store (i, j) and, for a symmetric problem, (j, i).  The
-//               second accumulator lets tile t+1's MMAs run meanwhile.
+//   warps 2-9   epilogue, two warps per TMEM lane quadrant (tcgen05.ld only
+//               reaches lanes 32*(warp%4)..+31), each taking 128 of the 256
+//               columns: load 16 accumulator columns at a time (one TMEM lane
+//               = one variable i per thread), derive n10, n01, n00, evaluate
+//               MI and store (i, j) as 16-byte vectors and, for a symmetric
+//               problem, (j, i) as coalesced rows.  The second accumulator
+//               lets tile t+1's MMAs run meanwhile.
 // Tiles come from a host-built list: for all-pairs only blocks that touch
 // the upper triangle (j >= i), in groups of column blocks so that CTAs running
 // at the same time share operand panels in L2.
 //
-// Every mbarrier wait is bounded (timeout_ns from its start, %globaltimer).  A role whose
-// wait runs out sets a bit in the device error word and a CTA-wide abort flag;
-// the other roles see the flag and unwind; the producer waits (bounded) for
-// its copies still in flight, the MMA thread for its MMAs, and warp 1 frees
-// the tensor memory before the CTA exits.
+// Every mbarrier wait is bounded (timeout_ns from its start, %globaltimer).
+// A role whose wait runs out sets a bit in the device error word and a
+// CTA-wide abort flag; the other roles see the flag and unwind; the producer
+// waits (bounded) for its copies still in flight, the MMA thread for its
+// MMAs, and warp 1 frees the tensor memory before the CTA exits.
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -37,33 +40,34 @@ namespace gbmi {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;    // 320
 constexpr int kUmmaK = 32;                       // K per MMA for 8-bit inputs
 constexpr int kABytes = kTcBM * kTcBK;           // 16 KB
 constexpr int kBBytes = kTcBN * kTcBK;           // 32 KB
 constexpr int kStageBytes = kABytes + kBBytes;   // 48 KB
 constexpr int kAccCols = kTcBN;                  // FP32 columns per accumulator
 constexpr int kTmemCols = 2 * kAccCols;          // 512: the whole tensor memory
-constexpr int kStageWords = 32 * 33;             // epilogue staging per warp (padded)
-constexpr int kEpiWarps = 4;
+constexpr int kColsPerWarp = kTcBN / 2;          // 128
+constexpr int kGroup = 16;                       // accumulator columns per tcgen05.ld
 
 constexpr size_t kOffStages = 0;
-constexpr size_t kOffStaging = kOffStages + static_cast<size_t>(kStages) * kStageBytes;
-constexpr size_t kOffBars = kOffStaging + static_cast<size_t>(kEpiWarps) * kStageWords * 4;
+constexpr size_t kOffColVars = kOffStages + static_cast<size_t>(kStages) * kStageBytes;
+constexpr size_t kColVarBytes = static_cast<size_t>(kColsPerWarp) * sizeof(MiVar);   // 4 KB
+constexpr size_t kOffBars = kOffColVars + kEpiWarps * kColVarBytes;
 constexpr int kNumBars = 2 * kStages + 4 + 1;    // full, empty, tmem full x2, tmem empty x2, drain
 constexpr size_t kOffMisc = kOffBars + kNumBars * 8;
 constexpr size_t kSmemBytes = 1024 + kOffMisc + 64;
 
 static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte alignment");
-static_assert(kOffBars % 8 == 0, "barriers need 8-byte alignment");
 static_assert(kSmemBytes <= 232448, "shared memory budget");
 
 struct Smem {
     uint8_t* base;
     __device__ uint8_t* a(int s) const { return base + kOffStages + s * kStageBytes; }
     __device__ uint8_t* b(int s) const { return base + kOffStages + s * kStageBytes + kABytes; }
-    __device__ uint32_t* staging(int w) const {
-        return reinterpret_cast<uint32_t*>(base + kOffStaging) + w * kStageWords;
+    __device__ MiVar* colvars(int e) const {
+        return reinterpret_cast<MiVar*>(base + kOffColVars + e * kColVarBytes);
     }
     __device__ uint64_t* bar(int k) const { return reinterpret_cast<uint64_t*>(base + kOffBars) + k; }
     __device__ uint32_t full(int s) const { return ptx::smem_u32(bar(s)); }
@@ -99,7 +103,8 @@ __device__ void run_producer(const Smem& sm, const CUtensorMap* tmA, const CUten
         const int yA = tile.x * kTcBM;
         const int yB = tile.y * kTcBN;
         for (int kb = 0; kb < a.k_blocks; ++kb) {
-            if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, a.timeout_ns, sm.abort_flag())) {
+            if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, a.timeout_ns,
+                                        sm.abort_flag())) {
                 raise_abort(sm, a.err, kErrTimeoutLoad);
                 ok = false;
                 break;
@@ -141,7 +146,8 @@ __device__ void run_mma(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
     uint32_t acc_phase = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
-        if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, a.timeout_ns, sm.abort_flag())) {
+        if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, a.timeout_ns,
+                                    sm.abort_flag())) {
             raise_abort(sm, a.err, kErrTimeoutMma);
             break;
         }
@@ -189,93 +195,174 @@ __device__ void run_mma(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
 
 // ------------------------------------------------------------------ epilogue
 template <int kMode>
+__device__ __forceinline__ void store_one(const TcArgs& a, int64_t row, int64_t col, uint32_t x) {
+    if (kMode == kTcModeMI) {
+        a.out_f[row * a.ld_out + col] = __uint_as_float(x);
+    } else if (kMode == kTcModeCounts) {
+        a.out_c[row * a.ld_out + col] = static_cast<int32_t>(x);
+    } else {
+        a.out_c[row * a.ld_out + col] += static_cast<int32_t>(x);
+    }
+}
+
+template <int kMode>
 __device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int lane_base = (warp & 3) * 32;   // TMEM lanes this warp may access
-    uint32_t* stg = sm.staging(warp - 2);
+    const int lane_base = (warp & 3) * 32;             // TMEM lanes this warp may access
+    const int col_base = ((warp - 2) >> 2) * kColsPerWarp;
+    MiVar* cv = sm.colvars(warp - 2);                  // this warp's column terms
+    const MiParams& P = a.mp;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
         const int2 tile = a.tiles[t];
         const int64_t ibase = static_cast<int64_t>(tile.x) * kTcBM + lane_base;
         const int64_t i = ibase + lane;
-        const int64_t jb = static_cast<int64_t>(tile.y) * kTcBN;
+        const int64_t jstart = static_cast<int64_t>(tile.y) * kTcBN + col_base;
+        const bool row_ok = i < a.n_a;
+        MiVar A;
+        A.v = 0;
+        A.r1 = A.r0 = A.rchi = 0.f;
+        A.h = 0.0;
+        A.unused = 0.0;
+        if (kMode == kTcModeMI) {
+            // stage the per-variable terms of this warp's 128 columns while the
+            // accumulator is still being produced
+            __syncwarp();
+            for (int k = lane; k < kColsPerWarp; k += 32) {
+                const int64_t j = jstart + k;
+                if (j < a.n_b) {
+                    cv[k] = load_var(a.vb + j);
+                } else {
+                    cv[k] = A;
+                }
+            }
+            if (row_ok) A = load_var(a.va + i);
+            __syncwarp();
+        }
         if (!ptx::mbar_wait_bounded(sm.tfull(acc), acc_phase, a.timeout_ns, sm.abort_flag())) {
             raise_abort(sm, a.err, kErrTimeoutEpilogue);
             break;
         }
         ptx::tc_fence_after();
-        const bool row_ok = i < a.n_a;
-        int64_t vi = 0;
-        double hi = 0.0;
-        if (kMode == kTcModeMI && row_ok) {
-            vi = a.va[i];
-            if (a.ha) hi = a.ha[i];
-        }
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(lane_base) << 16) +
-                               static_cast<uint32_t>(acc * kAccCols);
+                               static_cast<uint32_t>(acc * kAccCols + col_base);
 #pragma unroll 1
-        for (int c = 0; c < kTcBN; c += 32) {
-            const int64_t j0 = jb + c;
-            // warp-uniform skips: chunk beyond the last variable, or (symmetric)
+        for (int g = 0; g < kColsPerWarp; g += kGroup) {
+            const int64_t j0 = jstart + g;
+            // warp-uniform skips: group beyond the last variable, or (symmetric)
             // entirely below the diagonal for this warp's 32 rows
             if (j0 >= a.n_b) break;
-            if (a.symmetric && j0 + 31 < ibase) continue;
-            uint32_t r[32];
-            ptx::tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c), r);
+            if (a.symmetric && j0 + kGroup - 1 < ibase) continue;
+            uint32_t r[kGroup];
+            ptx::tmem_ld_32x32b_x16(taddr + static_cast<uint32_t>(g), r);
             ptx::tmem_wait_ld();
-            // park the 32 accumulator columns in this lane's column of the
-            // staging block; each lane only touches its own column until the
-            // __syncwarp below
+            if (kMode == kTcModeMI) {
+                // pass 1: FP32 MI, or a mark for the FP64 combine
+                uint32_t need64 = 0;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) stg[q * 33 + lane] = r[q];
-#pragma unroll 2
-            for (int q = 0; q < 32; ++q) {
-                const int64_t j = j0 + q;
-                const int32_t n11 = __float2int_rn(__uint_as_float(stg[q * 33 + lane]));
-                uint32_t val;
-                if (kMode == kTcModeMI) {
+                for (int q = 0; q < kGroup; ++q) {
+                    const int64_t j = j0 + q;
+                    const int32_t n11 = __float2int_rn(__uint_as_float(r[q]));
                     float mi = 0.f;
                     if (row_ok && j < a.n_b && (!a.symmetric || j >= i)) {
-                        const double hj = a.hb ? a.hb[j] : 0.0;
-                        mi = mi_pair(n11, vi, a.vb[j], hi, hj, a.mp);
+                        const MiVar B = cv[g + q];
+                        const MiCounts c = mi_counts(n11, A.v, B.v, P);
+                        if (c.det != 0) {
+                            const float fdet = static_cast<float>(c.det);
+                            bool small = P.fixup && mi_surely_small(fdet, A, B, P);
+                            if (!small) {
+                                mi = fmaxf(mi_fp32(c, fdet, A, B, P), 0.f);
+                                small = P.fixup && mi < P.fixup_below;
+                            }
+                            if (small) need64 |= 1u << q;
+                        }
                     }
-                    val = __float_as_uint(mi);
+                    r[q] = need64 & (1u << q) ? static_cast<uint32_t>(n11)
+                                              : __float_as_uint(mi);
+                }
+                // pass 2: FP64 n log n combine, table reads issued four pairs at a time
+                if (__any_sync(0xffffffffu, need64 != 0)) {
+#pragma unroll
+                    for (int q0 = 0; q0 < kGroup; q0 += 4) {
+                        double tv[4][4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = q0 + u;
+                            const bool on = (need64 >> q) & 1u;
+                            const int32_t n11 = on ? static_cast<int32_t>(r[q]) : 0;
+                            const int32_t vj = on ? cv[g + q].v : 0;
+                            const MiCounts c = on ? mi_counts(n11, A.v, vj, P)
+                                                  : MiCounts{0, 0, 0, 0, 0};
+                            tv[u][0] = P.T[c.n11];
+                            tv[u][1] = P.T[c.n00];
+                            tv[u][2] = P.T[c.n10];
+                            tv[u][3] = P.T[c.n01];
+                        }
+                        const double Tm = P.T[P.m];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = q0 + u;
+                            if ((need64 >> q) & 1u) {
+                                const double s = (tv[u][0] + tv[u][1]) + (tv[u][2] + tv[u][3]);
+                                const double rr = s + (Tm - (A.h + cv[g + q].h));
+                                r[q] = __float_as_uint(
+                                    fmaxf(static_cast<float>(rr) * P.inv_m, 0.f));
+                            }
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q)
+                    r[q] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[q])));
+            }
+            // (j, i): lanes hold consecutive i -> each store is one coalesced row segment
+            if (a.symmetric && row_ok) {
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) {
+                    const int64_t j = j0 + q;
+                    if (j < a.n_b && j > i) store_one<kMode>(a, j, i, r[q]);
+                }
+            }
+            // (i, j): 16 consecutive columns of this thread's row
+            if (!row_ok) continue;
+            const bool full = (j0 + kGroup <= a.n_b) && (!a.symmetric || j0 >= i);
+            if (full && a.vec_store) {
+                if (kMode == kTcModeMI) {
+                    float4* dst = reinterpret_cast<float4*>(a.out_f + i * a.ld_out + j0);
+#pragma unroll
+                    for (int q = 0; q < kGroup / 4; ++q)
+                        dst[q] = make_float4(__uint_as_float(r[4 * q]),
+                                             __uint_as_float(r[4 * q + 1]),
+                                             __uint_as_float(r[4 * q + 2]),
+                                             __uint_as_float(r[4 * q + 3]));
                 } else {
-                    val = static_cast<uint32_t>(n11);
-                }
-                stg[q * 33 + lane] = val;
-                // (j, i): lanes hold consecutive i -> coalesced rows of the output
-                if (a.symmetric && row_ok && j < a.n_b && j > i) {
-                    if (kMode == kTcModeMI) {
-                        a.out_f[j * a.ld_out + i] = __uint_as_float(val);
-                    } else if (kMode == kTcModeCounts) {
-                        a.out_c[j * a.ld_out + i] = static_cast<int32_t>(val);
-                    } else {
-                        a.out_c[j * a.ld_out + i] += static_cast<int32_t>(val);
+                    int4* dst = reinterpret_cast<int4*>(a.out_c + i * a.ld_out + j0);
+#pragma unroll
+                    for (int q = 0; q < kGroup / 4; ++q) {
+                        int4 v = make_int4(static_cast<int>(r[4 * q]),
+                                           static_cast<int>(r[4 * q + 1]),
+                                           static_cast<int>(r[4 * q + 2]),
+                                           static_cast<int>(r[4 * q + 3]));
+                        if (kMode == kTcModeCountsAdd) {
+                            const int4 o = dst[q];
+                            v.x += o.x;
+                            v.y += o.y;
+                            v.z += o.z;
+                            v.w += o.w;
+                        }
+                        dst[q] = v;
                     }
                 }
-            }
-            // (i, j): read the 32 x 32 block transposed so that each store
-            // instruction writes one contiguous row segment
-            __syncwarp();
-            const int64_t jj = j0 + lane;
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const int64_t ii = ibase + rr;
-                if (ii < a.n_a && jj < a.n_b && (!a.symmetric || jj >= ii)) {
-                    const uint32_t x = stg[lane * 33 + rr];
-                    if (kMode == kTcModeMI) {
-                        a.out_f[ii * a.ld_out + jj] = __uint_as_float(x);
-                    } else if (kMode == kTcModeCounts) {
-                        a.out_c[ii * a.ld_out + jj] = static_cast<int32_t>(x);
-                    } else {
-                        a.out_c[ii * a.ld_out + jj] += static_cast<int32_t>(x);
-                    }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) {
+                    const int64_t j = j0 + q;
+                    if (j < a.n_b && (!a.symmetric || j >= i)) store_one<kMode>(a, i, j, r[q]);
                 }
             }
-            __syncwarp();
         }
         ptx::tc_fence_before();
         ptx::mbar_arrive(sm.tempty(acc));

@@ -18,6 +18,8 @@ namespace gbmi {
 // Bp (popcount operand): one row per variable, bit (r % 32) of 32-bit word
 //    r / 32 holds sample r; wpr = ldp / 32 words per row, same row padding.
 // v  column counts, int32, one per variable.
+// MiVar per-variable epilogue terms (reciprocals, FP64 entropy term), one per
+//    variable, computed from v once per call.
 constexpr int64_t kRowPad = 256;
 constexpr int64_t kColPad = 128;
 
@@ -49,12 +51,11 @@ cudaError_t launch_validate(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
 // ----------------------------------------------------- elementwise kernels
 cudaError_t launch_zero_u32(void* p, int64_t words, cudaStream_t s);
 cudaError_t launch_nlogn_table(double* T, int64_t len, cudaStream_t s);
-cudaError_t launch_col_h(const int32_t* v, int64_t n, const MiParams& P, double* h,
-                         cudaStream_t s);
-cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const int32_t* va,
-                                  const int32_t* vb, const double* ha, const double* hb,
-                                  int64_t n1, int64_t n2, const MiParams& P, float* out,
-                                  int64_t ld_out, cudaStream_t s);
+cudaError_t launch_mi_vars(const int32_t* v, int64_t n, const MiParams& P, MiVar* out,
+                           cudaStream_t s);
+cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const MiVar* va,
+                                  const MiVar* vb, int64_t n1, int64_t n2, const MiParams& P,
+                                  float* out, int64_t ld_out, cudaStream_t s);
 
 // ---------------------------------------------------------- popcount Gram
 struct PopcArgs {
@@ -63,10 +64,8 @@ struct PopcArgs {
     int64_t wpr;         // words per row (multiple of 4)
     int64_t n_a, n_b;
     int symmetric;       // Ba == Bb: compute j >= i tiles, write both halves
-    const int32_t* va;
-    const int32_t* vb;
-    const double* ha;
-    const double* hb;
+    const MiVar* va;     // per-variable terms (MI output only)
+    const MiVar* vb;
     MiParams mp;
     float* out_f;        // MI output (or null)
     int32_t* out_c;      // counts output (or null)
@@ -89,10 +88,9 @@ struct TcArgs {
     int64_t n_a, n_b;    // valid variables of A and B
     int symmetric;       // A == B: write (i, j) and (j, i) for j >= i only
     int mode;            // TcMode
-    const int32_t* va;
-    const int32_t* vb;
-    const double* ha;
-    const double* hb;
+    int vec_store;       // output rows are 16-byte aligned (ld % 4 == 0, aligned base)
+    const MiVar* va;     // per-variable terms (MI mode)
+    const MiVar* vb;
     MiParams mp;
     float* out_f;
     int32_t* out_c;

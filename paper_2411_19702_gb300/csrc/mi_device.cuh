@@ -4,21 +4,31 @@
 //
 // Counts (Sec. 3.1, Eq. 6 and Eq. 7, with C_ij = v_j):
 //   n10 = v_i - n11,  n01 = v_j - n11,  n00 = m - v_i - v_j + n11.
-// MI (Eq. 1 / Eq. 2) in the determinant form: with det = n11*n00 - n10*n01,
-// every cell satisfies n_c*m - a_c*b_c = s_c*det (a_c, b_c its marginal
-// counts, s = +1 for 11/00 and -1 for 10/01), hence
-//   MI = 1/(m ln 2) * sum_{c: n_c > 0} n_c * ln(1 + s_c*det/(a_c*b_c)).
-// This has no cancellation near independence (det = 0 <=> MI = 0 exactly) and
-// its error scales with the dependence.  Cells with n_c = 0 contribute 0
-// (the 0*log 0 = 0 limit replaces the paper's epsilon).
+// MI (Eq. 1 / Eq. 2).  With det = n11*n00 - n10*n01 every cell satisfies
+// n_c*m - a_c*b_c = s_c*det (a_c, b_c its marginal counts, s = +1 for 11/00
+// and -1 for 10/01), i.e. n_c = (a_c b_c / m)(1 + x_c) with
+// x_c = s_c det / (a_c b_c).  Since sum_c s_c = 0, the linear terms cancel
+// exactly and
+//   m ln2 * MI = sum_c n_c ln(1 + x_c) = sum_c (a_c b_c / m) h(x_c),
+//   h(x) = (1 + x) ln(1 + x) - x = x^2/2 - x^3/6 + x^4/12 - ...  (>= 0).
+// Each cell is evaluated as
+//   |x_c| < 1/32:  (a_c b_c / m) * h(x_c) with the series to x^7 (truncation
+//                  below 4e-11 relative): no cancellation, no division, no log;
+//   otherwise:     n_c ln(1 + x_c) - s_c det / m, the log of the exact quotient
+//                  (log1pf, or logf of the ratio far below independence), and
+//                  0 * log 0 = 0 for an empty cell (the paper's epsilon).
+// det = 0 <=> MI = 0 exactly.
 //
-// FP64 combine: for pairs whose FP32 value is below 1e-4 the value is
-// recomputed from a table T[k] = k*log2(k) in FP64 (additions only):
+// FP64 combine (optional, GBMI_OPT_FIXUP): pairs whose FP32 value is below
+// 1e-4 are recomputed from a table T[k] = k*log2(k) in FP64 (additions only):
 //   m*MI = T[n11] + T[n10] + T[n01] + T[n00] - H_i - H_j + T[m],
 //   H_i = T[v_i] + T[m - v_i],
-// which follows from Eq. 1 by expanding the logarithm of the ratio.
+// which follows from Eq. 1 by expanding the logarithm of the ratio.  Pairs go
+// there without the FP32 evaluation when the chi-square bound already places
+// them below 1e-4: MI (nats) <= chi^2-divergence = det^2 / (v_i (m - v_i)
+// v_j (m - v_j)) (KL <= chi^2).
 //
-// Both forms are symmetric in (i, j) to the last bit: exchanging the two
+// All forms are symmetric in (i, j) to the last bit: exchanging the two
 // variables swaps the 10 and 01 cells and the operands of commutative
 // operations only, so MI(i, j) and MI(j, i) are the same float.
 #pragma once
@@ -28,14 +38,38 @@
 namespace gbmi {
 
 struct MiParams {
-    int64_t m;           // samples
+    int32_t m;           // samples (< 2^31)
     float fm;            // (float)m
     float inv_m_ln2;     // 1 / (m ln 2)
-    double inv_m;        // 1 / m
+    float inv_m;         // 1 / m
     int fixup;           // 1: FP64 combine for pairs whose FP32 value is below fixup_below
     float fixup_below;   // 1e-4
+    float chi_below;     // chi-square bound (nats) under which a pair goes straight to FP64
     const double* T;     // T[k] = k log2 k for k = 0..m, or nullptr: evaluate inline
 };
+
+// Per-variable quantities of one side of a pair (32 bytes, so that the first
+// four fields load as one 16-byte vector).
+struct __align__(16) MiVar {
+    int32_t v;     // ones of the variable
+    float r1;      // 1 / v            (0 if v == 0)
+    float r0;      // 1 / (m - v)      (0 if v == m)
+    float rchi;    // 1 / (v (m - v))  (0 if either is 0)
+    double h;      // T[v] + T[m - v] for the FP64 combine (0 when it is off)
+    double unused;
+};
+
+__device__ __forceinline__ MiVar load_var(const MiVar* p) {
+    MiVar r;
+    const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+    r.v = __float_as_int(f.x);
+    r.r1 = f.y;
+    r.r0 = f.z;
+    r.rchi = f.w;
+    r.h = __ldg(&p->h);
+    r.unused = 0.0;
+    return r;
+}
 
 // T[k] = k log2 k in FP64 (0 for k = 0, 1), from the table when there is one.
 __device__ __forceinline__ double nlog2n(int64_t k, const MiParams& P) {
@@ -44,50 +78,98 @@ __device__ __forceinline__ double nlog2n(int64_t k, const MiParams& P) {
     return k > 1 ? x * log2(x) : 0.0;
 }
 
-// n_c * ln(n_c * m / (a * b)) for one cell with n_c > 0 (so a, b > 0), from
-// the signed determinant sdet = s_c * det.
-__device__ __forceinline__ float mi_cell(int64_t nc, float sdet, float a, float b, float fm) {
-    const float ab = a * b;
-    const float x = sdet / ab;
-    float l;
-    if (x > -0.5f) {
-        l = log1pf(x);
-    } else {
-        // far below independence: the ratio itself is well conditioned
-        l = logf((static_cast<float>(nc) * fm) / ab);
-    }
-    return static_cast<float>(nc) * l;
+__device__ __forceinline__ MiVar mi_var(int32_t v, const MiParams& P) {
+    MiVar r;
+    r.v = v;
+    const float a1 = static_cast<float>(v), a0 = static_cast<float>(P.m - v);
+    r.r1 = v > 0 ? 1.0f / a1 : 0.f;
+    r.r0 = v < P.m ? 1.0f / a0 : 0.f;
+    r.rchi = r.r1 * r.r0;
+    r.h = P.fixup ? nlog2n(v, P) + nlog2n(static_cast<int64_t>(P.m) - v, P) : 0.0;
+    r.unused = 0.0;
+    return r;
 }
 
-__device__ __forceinline__ float mi_pair(int64_t n11, int64_t vi, int64_t vj, double hi,
-                                         double hj, const MiParams& P) {
-    const int64_t m = P.m;
-    const int64_t n10 = vi - n11;
-    const int64_t n01 = vj - n11;
-    const int64_t n00 = m - vi - vj + n11;
-    const int64_t det = n11 * n00 - n10 * n01;
-    if (det == 0) return 0.f;   // exact independence: every log ratio is 0
-    const float fdet = static_cast<float>(det);
-    const float ai = static_cast<float>(vi), a0 = static_cast<float>(m - vi);
-    const float bj = static_cast<float>(vj), b0 = static_cast<float>(m - vj);
-    float t11 = 0.f, t10 = 0.f, t01 = 0.f, t00 = 0.f;
-    if (n11 > 0) t11 = mi_cell(n11, fdet, ai, bj, P.fm);
-    if (n10 > 0) t10 = mi_cell(n10, -fdet, ai, b0, P.fm);
-    if (n01 > 0) t01 = mi_cell(n01, -fdet, a0, bj, P.fm);
-    if (n00 > 0) t00 = mi_cell(n00, fdet, a0, b0, P.fm);
-    float mi = ((t11 + t00) + (t10 + t01)) * P.inv_m_ln2;
-    if (P.fixup && mi < P.fixup_below) {
-        const double s = (nlog2n(n11, P) + nlog2n(n00, P)) + (nlog2n(n10, P) + nlog2n(n01, P));
-        const double r = (s + (nlog2n(m, P) - (hi + hj))) * P.inv_m;
-        mi = static_cast<float>(r);
+// Contribution of one cell to m ln2 * MI (see the header comment).
+// sdet = s_c det as float, rab = (1/a)(1/b).
+__device__ __forceinline__ float mi_cell(int32_t nc, float sdet, float rab, int32_t a, int32_t b,
+                                         const MiParams& P) {
+    const float x = sdet * rab;
+    if (fabsf(x) < 0.03125f) {
+        // h(x) = x^2 (1/2 - x/6 + x^2/12 - x^3/20 + x^4/30 - x^5/42)
+        float p = fmaf(x, -1.0f / 42.0f, 1.0f / 30.0f);
+        p = fmaf(x, p, -0.05f);
+        p = fmaf(x, p, 1.0f / 12.0f);
+        p = fmaf(x, p, -1.0f / 6.0f);
+        p = fmaf(x, p, 0.5f);
+        const float w = (static_cast<float>(a) * static_cast<float>(b)) * P.inv_m;
+        return w * ((x * x) * p);
     }
+    float t = 0.f;
+    if (nc > 0) {
+        const float ab = static_cast<float>(a) * static_cast<float>(b);
+        const float xe = sdet / ab;
+        const float l = xe > -0.5f ? log1pf(xe)
+                                   : logf((static_cast<float>(nc) * P.fm) / ab);
+        t = static_cast<float>(nc) * l;
+    }
+    return t - sdet * P.inv_m;
+}
+
+struct MiCounts {
+    int32_t n11, n10, n01, n00;
+    int64_t det;
+};
+
+__device__ __forceinline__ MiCounts mi_counts(int32_t n11, int32_t vi, int32_t vj,
+                                              const MiParams& P) {
+    MiCounts c;
+    c.n11 = n11;
+    c.n10 = vi - n11;
+    c.n01 = vj - n11;
+    c.n00 = P.m - vi - vj + n11;
+    c.det = static_cast<int64_t>(c.n11) * c.n00 - static_cast<int64_t>(c.n10) * c.n01;
+    return c;
+}
+
+// True when the chi-square bound places the pair below the FP64 threshold.
+__device__ __forceinline__ bool mi_surely_small(float fdet, const MiVar& A, const MiVar& B,
+                                                const MiParams& P) {
+    return (fdet * fdet) * (A.rchi * B.rchi) < P.chi_below;
+}
+
+// FP32 MI in bits (det != 0).
+__device__ __forceinline__ float mi_fp32(const MiCounts& c, float fdet, const MiVar& A,
+                                         const MiVar& B, const MiParams& P) {
+    const int32_t vi = A.v, vj = B.v;
+    const float t11 = mi_cell(c.n11, fdet, A.r1 * B.r1, vi, vj, P);
+    const float t10 = mi_cell(c.n10, -fdet, A.r1 * B.r0, vi, P.m - vj, P);
+    const float t01 = mi_cell(c.n01, -fdet, A.r0 * B.r1, P.m - vi, vj, P);
+    const float t00 = mi_cell(c.n00, fdet, A.r0 * B.r0, P.m - vi, P.m - vj, P);
+    return ((t11 + t00) + (t10 + t01)) * P.inv_m_ln2;
+}
+
+// FP64 n*log2(n) combine in bits.
+__device__ __forceinline__ float mi_fp64(const MiCounts& c, const MiVar& A, const MiVar& B,
+                                         const MiParams& P) {
+    const double s = (nlog2n(c.n11, P) + nlog2n(c.n00, P)) + (nlog2n(c.n10, P) + nlog2n(c.n01, P));
+    const double r = s + (nlog2n(P.m, P) - (A.h + B.h));
+    return static_cast<float>(r) * P.inv_m;
+}
+
+__device__ __forceinline__ float mi_pair(int32_t n11, const MiVar& A, const MiVar& B,
+                                         const MiParams& P) {
+    const MiCounts c = mi_counts(n11, A.v, B.v, P);
+    if (c.det == 0) return 0.f;   // exact independence: every log ratio is 0
+    const float fdet = static_cast<float>(c.det);
+    bool need64 = P.fixup && mi_surely_small(fdet, A, B, P);
+    float mi = 0.f;
+    if (!need64) {
+        mi = mi_fp32(c, fdet, A, B, P);
+        need64 = P.fixup && mi < P.fixup_below;
+    }
+    if (need64) mi = mi_fp64(c, A, B, P);
     return fmaxf(mi, 0.f);
-}
-
-// H_j = T[v_j] + T[m - v_j] for the FP64 combine (0 when it is off).
-__device__ __forceinline__ double mi_col_h(int64_t v, const MiParams& P) {
-    if (!P.fixup) return 0.0;
-    return nlog2n(v, P) + nlog2n(P.m - v, P);
 }
 
 }  // namespace gbmi

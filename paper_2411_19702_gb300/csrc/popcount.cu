@@ -76,8 +76,8 @@ popcount_gram_kernel(const PopcArgs a) {
     for (int x = 0; x < 4; ++x) {
         const int64_t i = ia + ty * 4 + x;
         if (i >= a.n_a) continue;
-        const int64_t vi = a.out_f ? a.va[i] : 0;
-        const double hi = (a.out_f && a.ha) ? a.ha[i] : 0.0;
+        MiVar A;
+        if (a.out_f) A = load_var(a.va + i);
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
             const int64_t j = jb + tx * 4 + y;
@@ -88,8 +88,7 @@ popcount_gram_kernel(const PopcArgs a) {
                 if (a.symmetric && j != i) a.out_c[j * a.ld_out + i] = acc[x][y];
             }
             if (a.out_f != nullptr) {
-                const double hj = a.hb ? a.hb[j] : 0.0;
-                const float mi = mi_pair(acc[x][y], vi, a.vb[j], hi, hj, a.mp);
+                const float mi = mi_pair(acc[x][y], A, load_var(a.vb + j), a.mp);
                 a.out_f[i * a.ld_out + j] = mi;
                 if (a.symmetric && j != i) a.out_f[j * a.ld_out + i] = mi;
             }

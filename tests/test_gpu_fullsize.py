@@ -57,9 +57,11 @@ def test_paper_scale_sampled_parity():
     pi = np.concatenate([pi, np.minimum(tg, sr), d])
     pj = np.concatenate([pj, np.maximum(tg, sr), d])
     err = _check_sampled(XT, out, tc, pi, pj)
-    # planted noisy copies carry strong MI
+    # planted noisy copies carry far more MI than unrelated pairs (a copy of a
+    # very sparse column is mostly flip noise, so only the medians are compared)
     planted = out[torch.from_numpy(tg).cuda(), torch.from_numpy(sr).cuda()]
-    assert float(planted.min()) > 0.01
+    unrelated = out[torch.from_numpy(pi[:20_000]).cuda(), torch.from_numpy(pj[:20_000]).cuda()]
+    assert float(planted.median()) > 100 * float(unrelated.median())
     print(f"paper scale: max |MI - oracle| over {len(pi)} pairs = {err:.3e}")
 
 

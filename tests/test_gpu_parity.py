@@ -66,9 +66,16 @@ def test_counts_cross_exact(path):
     assert np.array_equal(got.cpu().numpy(), n11)
 
 
+@pytest.fixture(params=[0, 1], ids=["fp32", "fp64combine"])
+def fixup(request):
+    gbmi.set_option(gbmi.OPT_FIXUP, request.param)
+    yield request.param
+    gbmi.set_option(gbmi.OPT_FIXUP, 0)
+
+
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("m,n", SHAPES)
-def test_mi_all_pairs_matches_oracle(path, m, n):
+def test_mi_all_pairs_matches_oracle(path, m, n, fixup):
     X = _data(m, n, 5)
     want, _ = oracle.mi_matrix(X)
     out = gbmi.mi_all_pairs(torch.from_numpy(X).cuda(), path=path)
@@ -80,7 +87,20 @@ def test_mi_all_pairs_matches_oracle(path, m, n):
 
 
 @pytest.mark.parametrize("path", PATHS)
-def test_mi_cross_matches_oracle(path):
+def test_small_mi_relative_accuracy(path, fixup):
+    """Near independence (most pairs of sparse data) the FP32 form has no
+    cancellation: small MI values keep their relative accuracy too."""
+    X = _data(20000, 300, 15, 0.01, 0.1)
+    want, _ = oracle.mi_matrix(X)
+    got = gbmi.mi_all_pairs(torch.from_numpy(X).cuda(), path=path).cpu().numpy()
+    sel = (want > 1e-7) & (want < 1e-4)
+    assert sel.sum() > 1000
+    rel = np.abs(got[sel].astype(np.float64) - want[sel]) / want[sel]
+    assert rel.max() <= 1e-4, rel.max()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_mi_cross_matches_oracle(path, fixup):
     X, Y = _data(1500, 290, 6), _data(1500, 77, 7)
     Y[:, 3] = X[:, 10]
     Y[:, 4] = 1 - X[:, 11]
@@ -91,7 +111,7 @@ def test_mi_cross_matches_oracle(path):
 
 
 @pytest.mark.parametrize("path", PATHS)
-def test_degenerate_columns(path):
+def test_degenerate_columns(path, fixup):
     m, n = 999, 260
     X = _data(m, n, 8)
     X[:, 0] = 0                      # constant zero
@@ -111,19 +131,23 @@ def test_degenerate_columns(path):
     assert abs(got[4, 5] - got[5, 5]) <= MI_TOL
 
 
-def test_paths_agree_and_fixup_matters_little():
+def test_paths_agree_with_and_without_fp64_combine():
     X = _data(5000, 300, 9, 0.01, 0.2)
     Xd = torch.from_numpy(X).cuda()
-    outs = {p: gbmi.mi_all_pairs(Xd, path=p).cpu().numpy() for p in PATHS}
-    for p in PATHS[1:]:
-        assert np.max(np.abs(outs[p] - outs["fused"])) <= 2 * MI_TOL
-    gbmi.set_option(gbmi.OPT_FIXUP, 0)
-    try:
-        nofix = gbmi.mi_all_pairs(Xd, path="fused").cpu().numpy()
-    finally:
-        gbmi.set_option(gbmi.OPT_FIXUP, 1)
     want, _ = oracle.mi_matrix(X)
-    assert np.max(np.abs(nofix.astype(np.float64) - want)) <= MI_TOL
+    outs = {}
+    for fx in (0, 1):
+        gbmi.set_option(gbmi.OPT_FIXUP, fx)
+        try:
+            for p in PATHS:
+                outs[(p, fx)] = gbmi.mi_all_pairs(Xd, path=p).cpu().numpy()
+        finally:
+            gbmi.set_option(gbmi.OPT_FIXUP, 0)
+    for key, got in outs.items():
+        assert np.max(np.abs(got.astype(np.float64) - want)) <= MI_TOL, key
+    for fx in (0, 1):
+        for p in PATHS[1:]:
+            assert np.max(np.abs(outs[(p, fx)] - outs[("fused", fx)])) <= 2 * MI_TOL
 
 
 def test_mi_from_counts_matches_oracle():
