@@ -98,6 +98,32 @@ gbmi_status mi_all_pairs_host(const uint8_t* X, int64_t m, int64_t n, float* out
 gbmi_status mi_cross_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
                           float* out);
 
+/* No-allocation variant of mi_all_pairs (the paper has no counterpart: this
+ * is a service to callers of the library, not part of the method).
+ *
+ * For callers that must not allocate device memory: a host framework that
+ * owns the device memory through its own pool, a latency-critical loop that
+ * cannot afford cudaFree's device-wide synchronisation, a process under a
+ * hard memory cap.  The call performs no cudaMalloc/cudaFree and calls no
+ * allocating library routine.  Its scratch (packed operand, column counts,
+ * per-variable terms, tile list, error word) is one 64 MiB array inside the
+ * library, held by every GPU that loads the library until the process exits.
+ *
+ * X (m x n uint8 0/1) and out (n x n FP32) are caller-owned device pointers,
+ * as for mi_all_pairs; the result is the fused tensor-core path's with the
+ * FP32 epilogue (GBMI_OPT_FIXUP is ignored).  Limits: 1 <= m <= 2^24, and
+ * n_pad(n) * m_pad(m) bytes of packed operand (n rounded up to 256, m to 128)
+ * plus about 36 n bytes must fit in 64 MiB; larger problems return
+ * GBMI_ERR_ARG with the required size in gbmi_last_error_string().
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.  The
+ * call runs on the library's current stream and returns after its work has
+ * finished (GBMI_ERR_TIMEOUT if a bounded device-side wait gave up).  Every
+ * call uses the same array: calls whose work overlaps on the GPU (from other
+ * host threads or streams) race and must not be issued. */
+gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t n, float* out);
+
 /* ------------------------------------------------------ counts and pieces */
 
 /* Co-occurrence counts N11 = X^T X (G11 of Sec. 2 step 2) as int32, n x n,

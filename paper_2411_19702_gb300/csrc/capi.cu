@@ -519,6 +519,8 @@ gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
 
 }  // namespace
 
+void set_last_error(const char* msg) { t_last_error = msg; }
+
 bool make_operand_tmap(CUtensorMap* tm, const uint8_t* P, int64_t rows_p, int64_t ldp,
                        int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();

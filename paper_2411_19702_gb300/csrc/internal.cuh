@@ -108,4 +108,7 @@ cudaError_t launch_gram_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const
 size_t gram_tc_smem_bytes();
 cudaError_t gram_tc_prepare();   // set the kernel's shared-memory attribute (current device)
 
+// Set the text gbmi_last_error_string() returns on this host thread.
+void set_last_error(const char* msg);
+
 }  // namespace gbmi

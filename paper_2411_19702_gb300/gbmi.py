@@ -73,6 +73,7 @@ def load(path: str | None = None):
             "gbmi_sync": [],
             "gbmi_shutdown": [],
             "gbmi_profile_reset": [],
+            "mi_all_pairs_noalloc": [vp, i64, i64, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -139,6 +140,25 @@ def mi_all_pairs(X, out=None, path="auto"):
         assert out.shape == (n, n) and out.dtype == torch.float32 and out.is_contiguous()
         lib = _bind_stream(X.device)
         _check(lib.gbmi_mi_all_pairs_path(X.data_ptr(), m, n, out.data_ptr(), _path(path)))
+    return out
+
+
+def mi_all_pairs_noalloc(X, out):
+    """All-pairs MI through the entry point that allocates no device memory.
+
+    For callers that cannot let the library allocate (their framework owns
+    the device memory, or a cudaFree's device-wide wait is not acceptable):
+    ``out`` (n x n float32, on X's device) must be provided; the library's
+    own scratch is a fixed 64 MiB array.  Returns when the result is written.
+    """
+    import torch
+    X = _prep(X)
+    m, n = X.shape
+    if out.shape != (n, n) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 (n, n) tensor")
+    with torch.cuda.device(X.device):
+        lib = _bind_stream(X.device)
+        _check(lib.mi_all_pairs_noalloc(X.data_ptr(), m, n, out.data_ptr()))
     return out
 
 
