@@ -67,7 +67,8 @@ typedef enum {
                                     so its consumer's bounded wait must run out (default 0)      */
     GBMI_OPT_GROUP_COLS = 4,     /* tile-order group width in 256-column blocks (default 8)      */
     GBMI_OPT_MAX_CTAS = 5,       /* cap on persistent CTAs, 0 = one per SM (default 0)           */
-    GBMI_OPT_PROFILE = 6         /* 1: time every kernel launch with CUDA events (default 0)     */
+    GBMI_OPT_PROFILE = 6,        /* 1: time every kernel launch with CUDA events (default 0)     */
+    GBMI_OPT_TILE_N = 7          /* tensor-core tile width 64/128/256; 0 = tuner / model (default) */
 } gbmi_option;
 
 /* ---------------------------------------------------------------- core calls */
@@ -173,6 +174,17 @@ uint64_t gbmi_launch_count(void);
 
 /* Free the workspace (waits for the device first). */
 gbmi_status gbmi_shutdown(void);
+
+/* Tile-width table of the autotuner (no counterpart in the paper).  The
+ * tensor-core Gram works on tiles of 128 x tile_n variable pairs; narrow tiles
+ * waste less padding on small n, wide tiles stream fewer operand bytes per
+ * pair.  gbmi_tuner_set records the best width measured for problems in the
+ * bucket of (m, n) (floor(log2 m), floor(2 log2 n)); gbmi_tile_n returns the
+ * width an all-pairs call of that shape would use (GBMI_OPT_TILE_N, else the
+ * table, else an operand-traffic cost model). */
+gbmi_status gbmi_tuner_set(int64_t m, int64_t n, int tile_n);
+gbmi_status gbmi_tuner_clear(void);
+int gbmi_tile_n(int64_t m, int64_t n);
 
 /* Per-kernel launch profile (enable with GBMI_OPT_PROFILE).  Each kernel
  * launch is bracketed by CUDA events on the library's stream;

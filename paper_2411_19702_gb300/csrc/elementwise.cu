@@ -31,6 +31,19 @@ __global__ void mi_vars_kernel(const int32_t* v, int64_t n, const MiParams P, Mi
         out[j] = mi_var(v[j], P);
 }
 
+__global__ void mi_vars_grouped_kernel(const int32_t* v, const int64_t* var_begin, int njobs,
+                                       int64_t total, const MiParams* params, MiVar* out) {
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = njobs - 1;   // last job whose first variable <= x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (var_begin[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        out[x] = mi_var(v[x], params[lo]);
+    }
+}
+
 // One thread per output element; a CTA covers 256 consecutive j of one row
 // block, so N11 reads and MI writes are coalesced and the row terms uniform.
 __global__ void mi_from_counts_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* va,
@@ -64,6 +77,16 @@ cudaError_t launch_mi_vars(const int32_t* v, int64_t n, const MiParams& P, MiVar
     const int64_t blocks = (n + 255) / 256;
     mi_vars_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(v, n, P,
                                                                                        out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mi_vars_grouped(const int32_t* v, const int64_t* var_begin, int njobs,
+                                   int64_t total, const MiParams* params, MiVar* out,
+                                   cudaStream_t s) {
+    if (njobs <= 0 || total <= 0) return cudaSuccess;
+    const int64_t blocks = (total + 255) / 256;
+    mi_vars_grouped_kernel<<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(
+        v, var_begin, njobs, total, params, out);
     return cudaGetLastError();
 }
 

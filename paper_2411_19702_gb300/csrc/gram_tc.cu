@@ -3,26 +3,31 @@
 // fused into the epilogue (the paper's "only one matrix multiplication",
 // Sec. 3.1, with everything after it done per tile while it is on chip).
 //
-// Operands: the packed matrix P (one row per variable, FP8 E4M3 0x00/0x38 per
-// sample).  0 and 1 are exact in E4M3, every product is 0 or 1 and the FP32
-// accumulator holds integers exactly below 2^24, so a tile's counts are exact
-// as long as one launch accumulates at most 2^24 samples (k_blocks * 128).
+// Operands: K-block-major packed matrices (for each block of 128 samples, one
+// 128-byte row per variable, FP8 E4M3 0x00/0x38).  0 and 1 are exact in
+// E4M3, every product is 0 or 1 and the FP32 accumulator holds integers
+// exactly below 2^24, so a tile's counts are exact as long as one launch
+// accumulates at most 2^24 samples (k_blocks * 128).  One launch can serve
+// many datasets: every tile names its job (dataset), whose descriptor gives
+// the operands' first rows in the shared buffer, its sample range, its tile
+// width bn (64, 128 or 256), its epilogue terms and its output.
 //
 // Persistent, warp-specialised CTA (320 threads, one CTA per SM):
-//   warp 0      TMA producer: 128 x 128-byte slice of A (variables of tile
-//               row I) and 256 x 128-byte slice of B (tile column J) per
-//               stage into a 4-stage shared-memory ring (128-byte swizzle).
+//   warp 0      TMA producer: per stage one 128 x 128-byte box of A (the
+//               variables of row block I) and one bn x 128-byte box of B
+//               (column block J) into a 4-stage shared-memory ring
+//               (128-byte swizzle).
 //   warp 1      allocates 512 TMEM columns; one thread issues
-//               tcgen05.mma.kind::f8f6f4 M=128 N=256 K=32 (4 per stage) into
+//               tcgen05.mma.kind::f8f6f4 M=128 N=bn K=32 (4 per stage) into
 //               one of two 256-column FP32 accumulators, commits each stage
 //               back to the ring and each finished tile to the epilogue.
 //   warps 2-9   epilogue, two warps per TMEM lane quadrant (tcgen05.ld only
-//               reaches lanes 32*(warp%4)..+31), each taking 128 of the 256
-//               columns: load 16 accumulator columns at a time (one TMEM lane
-//               = one variable i per thread), derive n10, n01, n00, evaluate
-//               MI and store (i, j) as 16-byte vectors and, for a symmetric
-//               problem, (j, i) as coalesced rows.  The second accumulator
-//               lets tile t+1's MMAs run meanwhile.
+//               reaches lanes 32*(warp%4)..+31), each taking bn/2 columns:
+//               load 16 accumulator columns at a time (one TMEM lane = one
+//               variable i per thread), derive n10, n01, n00, evaluate MI and
+//               store (i, j) as 16-byte vectors and, for a symmetric problem,
+//               (j, i) as coalesced rows.  The second accumulator lets tile
+//               t+1's MMAs run meanwhile.
 // Tiles come from a host-built list: for all-pairs only blocks that touch
 // the upper triangle (j >= i), in groups of column blocks so that CTAs running
 // at the same time share operand panels in L2.
@@ -32,6 +37,8 @@
 // CTA-wide abort flag; the other roles see the flag and unwind; the producer
 // waits (bounded) for its copies still in flight, the MMA thread for its
 // MMAs, and warp 1 frees the tensor memory before the CTA exits.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -44,16 +51,16 @@ constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;    // 320
 constexpr int kUmmaK = 32;                       // K per MMA for 8-bit inputs
 constexpr int kABytes = kTcBM * kTcBK;           // 16 KB
-constexpr int kBBytes = kTcBN * kTcBK;           // 32 KB
+constexpr int kBBytes = kTcBNMax * kTcBK;        // 32 KB (room for the widest tile)
 constexpr int kStageBytes = kABytes + kBBytes;   // 48 KB
-constexpr int kAccCols = kTcBN;                  // FP32 columns per accumulator
+constexpr int kAccCols = kTcBNMax;               // TMEM columns per accumulator buffer
 constexpr int kTmemCols = 2 * kAccCols;          // 512: the whole tensor memory
-constexpr int kColsPerWarp = kTcBN / 2;          // 128
+constexpr int kColsPerWarpMax = kTcBNMax / 2;    // 128
 constexpr int kGroup = 16;                       // accumulator columns per tcgen05.ld
 
 constexpr size_t kOffStages = 0;
 constexpr size_t kOffColVars = kOffStages + static_cast<size_t>(kStages) * kStageBytes;
-constexpr size_t kColVarBytes = static_cast<size_t>(kColsPerWarp) * sizeof(MiVar);   // 4 KB
+constexpr size_t kColVarBytes = static_cast<size_t>(kColsPerWarpMax) * sizeof(MiVar);   // 4 KB
 constexpr size_t kOffBars = kOffColVars + kEpiWarps * kColVarBytes;
 constexpr int kNumBars = 2 * kStages + 4 + 1;    // full, empty, tmem full x2, tmem empty x2, drain
 constexpr size_t kOffMisc = kOffBars + kNumBars * 8;
@@ -88,31 +95,41 @@ __device__ __forceinline__ void raise_abort(const Smem& sm, unsigned int* err, u
     *sm.abort_flag() = 1;
 }
 
+__device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
+    return L.jobs != nullptr ? L.jobs[j] : L.job0;
+}
+
 // ------------------------------------------------------------------ producer
-__device__ void run_producer(const Smem& sm, const CUtensorMap* tmA, const CUtensorMap* tmB,
-                             const TcArgs& a) {
+__device__ void run_producer(const Smem& sm, const OperandMaps& maps, const GramLaunch& L) {
     int pending_parity[kStages];
 #pragma unroll
     for (int s = 0; s < kStages; ++s) pending_parity[s] = -1;
-    if (a.debug_flags & 1) return;   // test hook: issue nothing, consumers must time out
+    if (L.debug_flags & 1) return;   // test hook: issue nothing, consumers must time out
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
-        const int2 tile = a.tiles[t];
-        const int yA = tile.x * kTcBM;
-        const int yB = tile.y * kTcBN;
-        for (int kb = 0; kb < a.k_blocks; ++kb) {
-            if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, a.timeout_ns,
+    for (int t = blockIdx.x; t < L.num_tiles && ok; t += gridDim.x) {
+        const GramTile tile = L.tiles[t];
+        const GramJob& job = job_of(L, tile.job);
+        const int bn = job.bn;
+        const CUtensorMap* mapB = bn == 256 ? &maps.box256 : (bn == 128 ? &maps.box128
+                                                                         : &maps.box64);
+        const uint32_t bytes = static_cast<uint32_t>((kTcBM + bn) * kTcBK);
+        const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * kTcBM;
+        const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn;
+        for (int kb = 0; kb < job.k_blocks; ++kb) {
+            if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, L.timeout_ns,
                                         sm.abort_flag())) {
-                raise_abort(sm, a.err, kErrTimeoutLoad);
+                raise_abort(sm, L.err, kErrTimeoutLoad);
                 ok = false;
                 break;
             }
-            ptx::mbar_arrive_expect_tx(sm.full(stage), kStageBytes);
-            const int x = (a.k_begin + kb) * kTcBK;
-            ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), tmA, sm.full(stage), x, yA);
-            ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), tmB, sm.full(stage), x, yB);
+            const int64_t k = job.k_begin + kb;
+            ptx::mbar_arrive_expect_tx(sm.full(stage), bytes);
+            ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.box128, sm.full(stage), 0,
+                             static_cast<int32_t>(a0 + k * job.strideA));
+            ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), mapB, sm.full(stage), 0,
+                             static_cast<int32_t>(b0 + k * job.strideB));
             pending_parity[stage] = static_cast<int>(phase);
             if (++stage == kStages) {
                 stage = 0;
@@ -129,7 +146,7 @@ __device__ void run_producer(const Smem& sm, const CUtensorMap* tmA, const CUten
             const uint32_t par = static_cast<uint32_t>(pending_parity[s]);
             while (!ptx::mbar_try_wait(bar, par)) {
                 if (ptx::globaltimer_ns() > d2) {
-                    atomicOr(a.err, kErrTimeoutDrain);
+                    atomicOr(L.err, kErrTimeoutDrain);
                     break;
                 }
             }
@@ -138,24 +155,27 @@ __device__ void run_producer(const Smem& sm, const CUtensorMap* tmA, const CUten
 }
 
 // ------------------------------------------------------------------ MMA issuer
-__device__ void run_mma(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
-    const uint32_t idesc = ptx::idesc_e4m3_f32(kTcBM, kTcBN);
+__device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base) {
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
-        if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, a.timeout_ns,
+    for (int t = blockIdx.x; t < L.num_tiles && ok; t += gridDim.x) {
+        const GramTile tile = L.tiles[t];
+        const GramJob& job = job_of(L, tile.job);
+        const uint32_t idesc = ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(job.bn));
+        const int k_blocks = job.k_blocks;
+        if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, L.timeout_ns,
                                     sm.abort_flag())) {
-            raise_abort(sm, a.err, kErrTimeoutMma);
+            raise_abort(sm, L.err, kErrTimeoutMma);
             break;
         }
         ptx::tc_fence_after();
         const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kAccCols);
-        for (int kb = 0; kb < a.k_blocks; ++kb) {
-            if (!ptx::mbar_wait_bounded(sm.full(stage), phase, a.timeout_ns, sm.abort_flag())) {
-                raise_abort(sm, a.err, kErrTimeoutMma);
+        for (int kb = 0; kb < k_blocks; ++kb) {
+            if (!ptx::mbar_wait_bounded(sm.full(stage), phase, L.timeout_ns, sm.abort_flag())) {
+                raise_abort(sm, L.err, kErrTimeoutMma);
                 ok = false;
                 break;
             }
@@ -187,7 +207,7 @@ __device__ void run_mma(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
     const uint64_t d2 = ptx::globaltimer_ns() + 100000000ull;
     while (!ptx::mbar_try_wait(sm.drain(), 0)) {
         if (ptx::globaltimer_ns() > d2) {
-            atomicOr(a.err, kErrTimeoutDrain);
+            atomicOr(L.err, kErrTimeoutDrain);
             break;
         }
     }
@@ -195,66 +215,72 @@ __device__ void run_mma(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
 
 // ------------------------------------------------------------------ epilogue
 template <int kMode>
-__device__ __forceinline__ void store_one(const TcArgs& a, int64_t row, int64_t col, uint32_t x) {
+__device__ __forceinline__ void store_one(const GramJob& g, int64_t row, int64_t col,
+                                          uint32_t x) {
     if (kMode == kTcModeMI) {
-        a.out_f[row * a.ld_out + col] = __uint_as_float(x);
+        g.out_f[row * g.ld_out + col] = __uint_as_float(x);
     } else if (kMode == kTcModeCounts) {
-        a.out_c[row * a.ld_out + col] = static_cast<int32_t>(x);
+        g.out_c[row * g.ld_out + col] = static_cast<int32_t>(x);
     } else {
-        a.out_c[row * a.ld_out + col] += static_cast<int32_t>(x);
+        g.out_c[row * g.ld_out + col] += static_cast<int32_t>(x);
     }
 }
 
 template <int kMode>
-__device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base) {
+__device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_base) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int lane_base = (warp & 3) * 32;             // TMEM lanes this warp may access
-    const int col_base = ((warp - 2) >> 2) * kColsPerWarp;
+    const int half = (warp - 2) >> 2;                  // which half of the tile's columns
     MiVar* cv = sm.colvars(warp - 2);                  // this warp's column terms
-    const MiParams& P = a.mp;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
-        const int2 tile = a.tiles[t];
-        const int64_t ibase = static_cast<int64_t>(tile.x) * kTcBM + lane_base;
+    for (int t = blockIdx.x; t < L.num_tiles; t += gridDim.x) {
+        const GramTile tile = L.tiles[t];
+        const GramJob& job = job_of(L, tile.job);
+        const MiParams& P = job.mp;
+        const int cols = job.bn >> 1;                  // columns of this warp
+        const int col_base = half * cols;
+        const int64_t n_a = job.n_a, n_b = job.n_b;
+        const bool sym = job.symmetric != 0;
+        const int64_t ibase = static_cast<int64_t>(tile.I) * kTcBM + lane_base;
         const int64_t i = ibase + lane;
-        const int64_t jstart = static_cast<int64_t>(tile.y) * kTcBN + col_base;
-        const bool row_ok = i < a.n_a;
+        const int64_t jstart = static_cast<int64_t>(tile.J) * job.bn + col_base;
+        const bool row_ok = i < n_a;
         MiVar A;
         A.v = 0;
         A.r1 = A.r0 = A.rchi = 0.f;
         A.h = 0.0;
         A.unused = 0.0;
         if (kMode == kTcModeMI) {
-            // stage the per-variable terms of this warp's 128 columns while the
+            // stage the per-variable terms of this warp's columns while the
             // accumulator is still being produced
             __syncwarp();
-            for (int k = lane; k < kColsPerWarp; k += 32) {
+            for (int k = lane; k < cols; k += 32) {
                 const int64_t j = jstart + k;
-                if (j < a.n_b) {
-                    cv[k] = load_var(a.vb + j);
+                if (j < n_b) {
+                    cv[k] = load_var(job.vb + j);
                 } else {
                     cv[k] = A;
                 }
             }
-            if (row_ok) A = load_var(a.va + i);
+            if (row_ok) A = load_var(job.va + i);
             __syncwarp();
         }
-        if (!ptx::mbar_wait_bounded(sm.tfull(acc), acc_phase, a.timeout_ns, sm.abort_flag())) {
-            raise_abort(sm, a.err, kErrTimeoutEpilogue);
+        if (!ptx::mbar_wait_bounded(sm.tfull(acc), acc_phase, L.timeout_ns, sm.abort_flag())) {
+            raise_abort(sm, L.err, kErrTimeoutEpilogue);
             break;
         }
         ptx::tc_fence_after();
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(lane_base) << 16) +
                                static_cast<uint32_t>(acc * kAccCols + col_base);
 #pragma unroll 1
-        for (int g = 0; g < kColsPerWarp; g += kGroup) {
+        for (int g = 0; g < cols; g += kGroup) {
             const int64_t j0 = jstart + g;
             // warp-uniform skips: group beyond the last variable, or (symmetric)
             // entirely below the diagonal for this warp's 32 rows
-            if (j0 >= a.n_b) break;
-            if (a.symmetric && j0 + kGroup - 1 < ibase) continue;
+            if (j0 >= n_b) break;
+            if (sym && j0 + kGroup - 1 < ibase) continue;
             uint32_t r[kGroup];
             ptx::tmem_ld_32x32b_x16(taddr + static_cast<uint32_t>(g), r);
             ptx::tmem_wait_ld();
@@ -266,7 +292,7 @@ __device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base
                     const int64_t j = j0 + q;
                     const int32_t n11 = __float2int_rn(__uint_as_float(r[q]));
                     float mi = 0.f;
-                    if (row_ok && j < a.n_b && (!a.symmetric || j >= i)) {
+                    if (row_ok && j < n_b && (!sym || j >= i)) {
                         const MiVar B = cv[g + q];
                         const MiCounts c = mi_counts(n11, A.v, B.v, P);
                         if (c.det != 0) {
@@ -295,12 +321,12 @@ __device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base
                             const int32_t vj = on ? cv[g + q].v : 0;
                             const MiCounts c = on ? mi_counts(n11, A.v, vj, P)
                                                   : MiCounts{0, 0, 0, 0, 0};
-                            tv[u][0] = P.T[c.n11];
-                            tv[u][1] = P.T[c.n00];
-                            tv[u][2] = P.T[c.n10];
-                            tv[u][3] = P.T[c.n01];
+                            tv[u][0] = nlog2n(c.n11, P);
+                            tv[u][1] = nlog2n(c.n00, P);
+                            tv[u][2] = nlog2n(c.n10, P);
+                            tv[u][3] = nlog2n(c.n01, P);
                         }
-                        const double Tm = P.T[P.m];
+                        const double Tm = nlog2n(P.m, P);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int q = q0 + u;
@@ -319,19 +345,19 @@ __device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base
                     r[q] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[q])));
             }
             // (j, i): lanes hold consecutive i -> each store is one coalesced row segment
-            if (a.symmetric && row_ok) {
+            if (sym && row_ok) {
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q) {
                     const int64_t j = j0 + q;
-                    if (j < a.n_b && j > i) store_one<kMode>(a, j, i, r[q]);
+                    if (j < n_b && j > i) store_one<kMode>(job, j, i, r[q]);
                 }
             }
             // (i, j): 16 consecutive columns of this thread's row
             if (!row_ok) continue;
-            const bool full = (j0 + kGroup <= a.n_b) && (!a.symmetric || j0 >= i);
-            if (full && a.vec_store) {
+            const bool full = (j0 + kGroup <= n_b) && (!sym || j0 >= i);
+            if (full && job.vec_store) {
                 if (kMode == kTcModeMI) {
-                    float4* dst = reinterpret_cast<float4*>(a.out_f + i * a.ld_out + j0);
+                    float4* dst = reinterpret_cast<float4*>(job.out_f + i * job.ld_out + j0);
 #pragma unroll
                     for (int q = 0; q < kGroup / 4; ++q)
                         dst[q] = make_float4(__uint_as_float(r[4 * q]),
@@ -339,7 +365,7 @@ __device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base
                                              __uint_as_float(r[4 * q + 2]),
                                              __uint_as_float(r[4 * q + 3]));
                 } else {
-                    int4* dst = reinterpret_cast<int4*>(a.out_c + i * a.ld_out + j0);
+                    int4* dst = reinterpret_cast<int4*>(job.out_c + i * job.ld_out + j0);
 #pragma unroll
                     for (int q = 0; q < kGroup / 4; ++q) {
                         int4 v = make_int4(static_cast<int>(r[4 * q]),
@@ -360,7 +386,7 @@ __device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q) {
                     const int64_t j = j0 + q;
-                    if (j < a.n_b && (!a.symmetric || j >= i)) store_one<kMode>(a, i, j, r[q]);
+                    if (j < n_b && (!sym || j >= i)) store_one<kMode>(job, i, j, r[q]);
                 }
             }
         }
@@ -375,8 +401,7 @@ __device__ void run_epilogue(const Smem& sm, const TcArgs& a, uint32_t tmem_base
 
 template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const TcArgs a) {
+gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__ GramLaunch L) {
     extern __shared__ uint8_t smem_raw[];
     Smem sm;
     sm.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -398,8 +423,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         ptx::fence_barrier_init();
     }
     if (warp == 0 && lane == 0) {
-        ptx::tma_prefetch_desc(&tmA);
-        ptx::tma_prefetch_desc(&tmB);
+        ptx::tma_prefetch_desc(&maps.box64);
+        ptx::tma_prefetch_desc(&maps.box128);
+        ptx::tma_prefetch_desc(&maps.box256);
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(sm.tmem_holder()), kTmemCols);
@@ -411,13 +437,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t tmem_base = *sm.tmem_holder();
 
     if (warp == 0) {
-        if (lane == 0) run_producer(sm, &tmA, &tmB, a);
+        if (lane == 0) run_producer(sm, maps, L);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) run_mma(sm, a, tmem_base);
+        if (lane == 0) run_mma(sm, L, tmem_base);
         __syncwarp();
     } else {
-        run_epilogue<kMode>(sm, a, tmem_base);
+        run_epilogue<kMode>(sm, L, tmem_base);
     }
 
     ptx::tc_fence_before();
@@ -447,20 +473,42 @@ cudaError_t gram_tc_prepare() {
                                 static_cast<int>(kSmemBytes));
 }
 
-cudaError_t launch_gram_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a,
-                           int grid, cudaStream_t s) {
-    if (a.num_tiles <= 0 || grid <= 0) return cudaSuccess;
-    if (a.k_blocks <= 0 || static_cast<int64_t>(a.k_blocks) * kTcBK > (int64_t{1} << 24))
-        return cudaErrorInvalidValue;
-    switch (a.mode) {
+int64_t gram_tile_count(int64_t n_a, int64_t n_b, int bn, bool symmetric) {
+    const int64_t TI = (n_a + kTcBM - 1) / kTcBM, TJ = (n_b + bn - 1) / bn;
+    if (!symmetric) return TI * TJ;
+    int64_t c = 0;
+    for (int64_t J = 0; J < TJ; ++J)   // row blocks I with 128 I <= bn J + bn - 1
+        c += std::min<int64_t>(TI, (J * bn + bn - 1) / kTcBM + 1);
+    return c;
+}
+
+void gram_tiles(int job, int64_t n_a, int64_t n_b, int bn, bool symmetric, int group_cols,
+                GramTile* out) {
+    const int64_t TI = (n_a + kTcBM - 1) / kTcBM, TJ = (n_b + bn - 1) / bn;
+    const int64_t group = std::max(1, group_cols);
+    int64_t k = 0;
+    for (int64_t g0 = 0; g0 < TJ; g0 += group) {
+        const int64_t g1 = std::min<int64_t>(TJ, g0 + group);
+        for (int64_t I = 0; I < TI; ++I)
+            for (int64_t J = g0; J < g1; ++J) {
+                if (symmetric && I * kTcBM > J * bn + bn - 1) continue;   // below the diagonal
+                out[k++] = GramTile{job, static_cast<int32_t>(I), static_cast<int32_t>(J), 0};
+            }
+    }
+}
+
+cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int grid,
+                           cudaStream_t s) {
+    if (L.num_tiles <= 0 || grid <= 0) return cudaSuccess;
+    switch (L.mode) {
         case kTcModeMI:
-            gram_tc_kernel<kTcModeMI><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, a);
+            gram_tc_kernel<kTcModeMI><<<grid, kThreads, kSmemBytes, s>>>(maps, L);
             break;
         case kTcModeCounts:
-            gram_tc_kernel<kTcModeCounts><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, a);
+            gram_tc_kernel<kTcModeCounts><<<grid, kThreads, kSmemBytes, s>>>(maps, L);
             break;
         case kTcModeCountsAdd:
-            gram_tc_kernel<kTcModeCountsAdd><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, a);
+            gram_tc_kernel<kTcModeCountsAdd><<<grid, kThreads, kSmemBytes, s>>>(maps, L);
             break;
         default:
             return cudaErrorInvalidValue;

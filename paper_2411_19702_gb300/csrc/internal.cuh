@@ -12,9 +12,13 @@ namespace gbmi {
 
 // ------------------------------------------------------------ packed layouts
 //
-// P  (tensor-core operand): one row per variable, one byte per sample, FP8
-//    E4M3 bit patterns 0x00 (0) and 0x38 (1.0).  rows_p = n rounded up to 256,
-//    ldp = m rounded up to 128 bytes; padding rows and columns are zero.
+// P  (tensor-core operand), K-block-major: for every block of 128 samples,
+//    one 128-byte row per variable (FP8 E4M3 0x00 / 0x38 = 1.0 per sample):
+//    byte (variable j, sample r) is at P[((r / 128) * rows_p + j) * 128 + r % 128].
+//    rows_p = n rounded up to 256, k_blocks = m rounded up to 128, / 128.
+//    Padding rows and samples are zero.  Any number of operands can share one
+//    buffer (each at its own first row), so one 2-D TMA descriptor of width
+//    128 bytes reaches every tile of every dataset.
 // Bp (popcount operand): one row per variable, bit (r % 32) of 32-bit word
 //    r / 32 holds sample r; wpr = ldp / 32 words per row, same row padding.
 // v  column counts, int32, one per variable.
@@ -36,15 +40,24 @@ enum : uint32_t {
 };
 
 // -------------------------------------------------------------- pack kernel
-struct PackArgs {
-    const uint8_t* X;
+struct PackJob {
+    const uint8_t* X;    // m x n, leading dimension ldx
     int64_t m, n, ldx;
-    uint8_t* P;        // may be null
+    uint8_t* P;          // K-block-major FP8 operand (this job's first row), or null
+    uint32_t* Bp;        // bit-packed operand, rows_p x (ldp / 32) words, or null
+    int32_t* v;          // column counts (zeroed before the launch), or null
     int64_t rows_p, ldp;
-    uint32_t* Bp;      // may be null; rows_p x (ldp / 32) words
-    int32_t* v;        // must be zeroed before the launch; may be null
+    int64_t cta_begin;   // first CTA of this job in a grouped launch
+    int32_t gx;          // column blocks of 128 variables (rows_p / 128)
+    int32_t tpc;         // 128-sample tiles walked by one CTA
+    int32_t vec;         // 16-byte loads of X allowed
+    int32_t pad;
 };
-cudaError_t launch_pack(const PackArgs& a, cudaStream_t s);
+// Fill the launch fields (gx, tpc, vec) of a job; returns its CTA count.
+int64_t pack_job_ctas(PackJob& j);
+cudaError_t launch_pack(const PackJob& job, cudaStream_t s);
+cudaError_t launch_pack_grouped(const PackJob* jobs, int njobs, int64_t total_ctas,
+                                cudaStream_t s);
 cudaError_t launch_validate(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
                             unsigned int* flag, cudaStream_t s);
 
@@ -53,6 +66,11 @@ cudaError_t launch_zero_u32(void* p, int64_t words, cudaStream_t s);
 cudaError_t launch_nlogn_table(double* T, int64_t len, cudaStream_t s);
 cudaError_t launch_mi_vars(const int32_t* v, int64_t n, const MiParams& P, MiVar* out,
                            cudaStream_t s);
+// Grouped: variables [var_begin[k], var_begin[k+1]) belong to dataset k, whose
+// parameters are params[k]; v and out are indexed by the flat variable index.
+cudaError_t launch_mi_vars_grouped(const int32_t* v, const int64_t* var_begin, int njobs,
+                                   int64_t total, const MiParams* params, MiVar* out,
+                                   cudaStream_t s);
 cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const MiVar* va,
                                   const MiVar* vb, int64_t n1, int64_t n2, const MiParams& P,
                                   float* out, int64_t ld_out, cudaStream_t s);
@@ -75,36 +93,58 @@ cudaError_t launch_popcount(const PopcArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------- tcgen05 FP8 Gram
 constexpr int kTcBM = 128;     // A rows per tile = TMEM lanes
-constexpr int kTcBN = 256;     // B rows per tile = accumulator columns
-constexpr int kTcBK = 128;     // K bytes per pipeline stage (one 128-byte swizzle row)
+constexpr int kTcBNMax = 256;  // largest B rows per tile = accumulator columns
+constexpr int kTcBK = 128;     // samples (bytes) per pipeline stage = one operand row
 
 enum TcMode : int { kTcModeMI = 0, kTcModeCounts = 1, kTcModeCountsAdd = 2 };
 
-struct TcArgs {
-    const int2* tiles;   // (I, J) per tile: A rows [128 I, 128 I + 128), B rows [256 J, ...)
-    int num_tiles;
-    int k_begin;         // first K block (units of 128 samples)
-    int k_blocks;        // K blocks to accumulate (k_blocks * 128 <= 2^24: exact FP32 counts)
-    int64_t n_a, n_b;    // valid variables of A and B
-    int symmetric;       // A == B: write (i, j) and (j, i) for j >= i only
-    int mode;            // TcMode
-    int vec_store;       // output rows are 16-byte aligned (ld % 4 == 0, aligned base)
-    const MiVar* va;     // per-variable terms (MI mode)
+// One dataset (or one cross pair) of a Gram launch.
+struct GramJob {
+    int64_t rowA, rowB;        // tensor-map row of (K block 0, variable 0) of A and B
+    int64_t strideA, strideB;  // rows between consecutive K blocks (rows_p of A / B)
+    int32_t k_begin;           // first K block accumulated by this launch
+    int32_t k_blocks;          // K blocks (k_blocks * 128 <= 2^24: exact FP32 counts)
+    int32_t n_a, n_b;          // valid variables of A and B
+    int32_t symmetric;         // A == B: write (i, j) and (j, i) for j >= i only
+    int32_t bn;                // B rows per tile: 64, 128 or 256
+    int32_t vec_store;         // output rows are 16-byte aligned
+    int32_t pad;
+    const MiVar* va;           // per-variable terms (MI mode)
     const MiVar* vb;
-    MiParams mp;
     float* out_f;
     int32_t* out_c;
     int64_t ld_out;
+    MiParams mp;
+};
+
+// One 128 x bn output tile: job index, row block I, column block J.
+struct GramTile {
+    int32_t job, I, J, pad;
+};
+
+struct GramLaunch {
+    const GramJob* jobs;       // device table, or null: every tile uses job0
+    GramJob job0;
+    const GramTile* tiles;
+    int num_tiles;
+    int mode;                  // TcMode
     unsigned int* err;
     uint64_t timeout_ns;
     int debug_flags;
 };
-// Encode the TMA descriptor of a packed operand P viewed as box_rows x 128-byte
-// tiles (128-byte swizzle).
-bool make_operand_tmap(CUtensorMap* tm, const uint8_t* P, int64_t rows_p, int64_t ldp,
-                       int box_rows);
-cudaError_t launch_gram_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a,
-                           int grid, cudaStream_t s);
+
+// TMA descriptors of a K-block-major operand buffer of total_rows rows of 128
+// bytes, for boxes of 64, 128 and 256 rows (128-byte swizzle).
+struct OperandMaps {
+    CUtensorMap box64, box128, box256;
+};
+bool make_operand_maps(OperandMaps* maps, const uint8_t* P, int64_t total_rows);
+// Tiles of one job in the kernel's order (groups of group_cols column blocks).
+int64_t gram_tile_count(int64_t n_a, int64_t n_b, int bn, bool symmetric);
+void gram_tiles(int job, int64_t n_a, int64_t n_b, int bn, bool symmetric, int group_cols,
+                GramTile* out);
+cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int grid,
+                           cudaStream_t s);
 size_t gram_tc_smem_bytes();
 cudaError_t gram_tc_prepare();   // set the kernel's shared-memory attribute (current device)
 

@@ -25,8 +25,7 @@
 // the error word) on every call.  Two calls whose work overlaps on the GPU
 // (other host threads, other streams) race on the array.  The call waits for
 // its own work before returning, so sequential calls from one thread are safe.
-#include <cudaTypedefs.h>
-
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -40,6 +39,8 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t{64} << 20;   // 64 MiB
 constexpr int kMaxDev = 64;
+constexpr int kTileN = 256;                          // tile width used by this entry point
+constexpr int kGroupCols = 8;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
@@ -56,18 +57,16 @@ gbmi_status na_fail(gbmi_status s, const std::string& msg) {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-// Grouped upper-triangle tile order of the fused kernel (groups of 8 column
-// blocks, all row blocks of a group before the next group), written by one
-// thread into the scratch array.
-__global__ void noalloc_tiles_kernel(int2* tiles, int TI, int TJ, int group) {
+// The fused kernel's upper-triangle tile order (groups of column blocks, all
+// row blocks of a group before the next group), written by one thread.
+__global__ void noalloc_tiles_kernel(GramTile* tiles, int TI, int TJ, int bn, int group) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     int k = 0;
     for (int g0 = 0; g0 < TJ; g0 += group) {
         const int g1 = min(TJ, g0 + group);
-        const int i_end = min(TI, 2 * g1);
-        for (int I = 0; I < i_end; ++I)
+        for (int I = 0; I < TI; ++I)
             for (int J = g0; J < g1; ++J)
-                if (I <= 2 * J + 1) tiles[k++] = make_int2(I, J);
+                if (I * kTcBM <= J * bn + bn - 1) tiles[k++] = GramTile{0, I, J, 0};
     }
 }
 
@@ -98,32 +97,6 @@ gbmi_status na_setup(int* dev_out) {
     return GBMI_OK;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 na_encode() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (fn == nullptr) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-bool na_tmap(CUtensorMap* tm, const uint8_t* P, int64_t rows_p, int64_t ldp, int box_rows) {
-    PFN_cuTensorMapEncodeTiled_v12000 fn = na_encode();
-    if (fn == nullptr) return false;
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(ldp), static_cast<cuuint64_t>(rows_p)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldp)};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(kTcBK), static_cast<cuuint32_t>(box_rows)};
-    cuuint32_t estr[2] = {1, 1};
-    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(P), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-           CUDA_SUCCESS;
-}
-
 }  // namespace
 }  // namespace gbmi
 
@@ -137,18 +110,16 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     if (n < 1 || n > (int64_t{1} << 20)) return na_fail(GBMI_ERR_ARG, "n out of range");
 
     // scratch layout: error word | v | per-variable terms | tile list | packed operand
-    const int64_t rows_p = pack_rows(n), ldp = pack_ld(m);
+    const int64_t rows_p = pack_rows(n), kb = pack_ld(m) / kTcBK;
     const int TI = static_cast<int>((n + kTcBM - 1) / kTcBM);
-    const int TJ = static_cast<int>((n + kTcBN - 1) / kTcBN);
-    const int group = 8;
-    int64_t ntiles = 0;
-    for (int J = 0; J < TJ; ++J) ntiles += std::min<int64_t>(TI, 2 * J + 2);
+    const int TJ = static_cast<int>((n + kTileN - 1) / kTileN);
+    const int64_t ntiles = gram_tile_count(n, n, kTileN, true);
     const size_t off_err = 0;
     const size_t off_v = off_err + 256;
     const size_t off_var = off_v + align256(static_cast<size_t>(n) * 4);
     const size_t off_tiles = off_var + align256(static_cast<size_t>(n) * sizeof(MiVar));
-    const size_t off_p = off_tiles + align256(static_cast<size_t>(ntiles) * sizeof(int2));
-    const size_t need = off_p + static_cast<size_t>(rows_p) * static_cast<size_t>(ldp);
+    const size_t off_p = off_tiles + align256(static_cast<size_t>(ntiles) * sizeof(GramTile));
+    const size_t need = off_p + static_cast<size_t>(kb * rows_p) * kTcBK;
     if (need > kScratchBytes)
         return na_fail(GBMI_ERR_ARG, "problem needs " + std::to_string(need) +
                                          " bytes of scratch; mi_all_pairs_noalloc holds " +
@@ -164,7 +135,7 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     unsigned int* err = reinterpret_cast<unsigned int*>(base + off_err);
     int32_t* v = reinterpret_cast<int32_t*>(base + off_v);
     MiVar* vars = reinterpret_cast<MiVar*>(base + off_var);
-    int2* tiles = reinterpret_cast<int2*>(base + off_tiles);
+    GramTile* tiles = reinterpret_cast<GramTile*>(base + off_tiles);
     uint8_t* P = base + off_p;
     cudaStream_t s = static_cast<cudaStream_t>(gbmi_get_stream());
 
@@ -172,17 +143,17 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     cudaError_t e = cudaMemsetAsync(base, 0, off_var, s);
     if (e != cudaSuccess) return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
 
-    PackArgs pa;
-    std::memset(&pa, 0, sizeof(pa));
-    pa.X = X;
-    pa.m = m;
-    pa.n = n;
-    pa.ldx = n;
-    pa.P = P;
-    pa.rows_p = rows_p;
-    pa.ldp = ldp;
-    pa.v = v;
-    if ((e = launch_pack(pa, s)) != cudaSuccess) return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
+    PackJob pj;
+    std::memset(&pj, 0, sizeof(pj));
+    pj.X = X;
+    pj.m = m;
+    pj.n = n;
+    pj.ldx = n;
+    pj.P = P;
+    pj.v = v;
+    pj.rows_p = rows_p;
+    pj.ldp = kb * kTcBK;
+    if ((e = launch_pack(pj, s)) != cudaSuccess) return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
 
     MiParams mp;
     mp.m = static_cast<int32_t>(m);
@@ -195,32 +166,39 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     mp.T = nullptr;
     if ((e = launch_mi_vars(v, n, mp, vars, s)) != cudaSuccess)
         return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
-    noalloc_tiles_kernel<<<1, 1, 0, s>>>(tiles, TI, TJ, group);
+    noalloc_tiles_kernel<<<1, 1, 0, s>>>(tiles, TI, TJ, kTileN, kGroupCols);
     if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
 
-    CUtensorMap tmA, tmB;
-    if (!na_tmap(&tmA, P, rows_p, ldp, kTcBM) || !na_tmap(&tmB, P, rows_p, ldp, kTcBN))
+    OperandMaps maps;
+    if (!make_operand_maps(&maps, P, kb * rows_p))
         return na_fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    TcArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.tiles = tiles;
-    a.num_tiles = static_cast<int>(ntiles);
-    a.k_begin = 0;
-    a.k_blocks = static_cast<int>(ldp / kTcBK);
-    a.n_a = n;
-    a.n_b = n;
-    a.symmetric = 1;
-    a.mode = kTcModeMI;
-    a.vec_store = (n % 4 == 0 && oa % 16 == 0) ? 1 : 0;
-    a.va = vars;
-    a.vb = vars;
-    a.mp = mp;
-    a.out_f = out;
-    a.ld_out = n;
-    a.err = err;
-    a.timeout_ns = 2000000000ull;
+    GramLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    GramJob& g = L.job0;
+    g.rowA = 0;
+    g.rowB = 0;
+    g.strideA = rows_p;
+    g.strideB = rows_p;
+    g.k_begin = 0;
+    g.k_blocks = static_cast<int32_t>(kb);
+    g.n_a = static_cast<int32_t>(n);
+    g.n_b = static_cast<int32_t>(n);
+    g.symmetric = 1;
+    g.bn = kTileN;
+    g.vec_store = (n % 4 == 0 && oa % 16 == 0) ? 1 : 0;
+    g.va = vars;
+    g.vb = vars;
+    g.out_f = out;
+    g.ld_out = n;
+    g.mp = mp;
+    L.jobs = nullptr;
+    L.tiles = tiles;
+    L.num_tiles = static_cast<int>(ntiles);
+    L.mode = kTcModeMI;
+    L.err = err;
+    L.timeout_ns = 2000000000ull;
     const int grid = static_cast<int>(std::min<int64_t>(g_na_sms[dev], ntiles));
-    if ((e = launch_gram_tc(tmA, tmB, a, grid, s)) != cudaSuccess)
+    if ((e = launch_gram_tc(maps, L, grid, s)) != cudaSuccess)
         return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
 
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess)

@@ -1,14 +1,17 @@
 // Pack pass: one read of X (m samples x n variables, row-major uint8) writes
-//   P  - the transposed FP8 operand of the tensor-core Gram (one row per
-//        variable, 0x00 / 0x38 = E4M3 1.0 per sample), padding zeroed,
+//   P  - the transposed FP8 operand of the tensor-core Gram in K-block-major
+//        order (for each block of 128 samples, one 128-byte row per variable;
+//        0x00 / 0x38 = E4M3 1.0 per sample), padding zeroed,
 //   Bp - the transposed bit-packed operand of the popcount Gram,
 //   v  - the column counts v_j = sum_r X_rj (Sec. 3.1, Term 2: v = D^T 1;
 //        also the diagonal of G11, Sec. 2 step 3).
 // The complement matrix of Sec. 2 step 1 is never formed: Eq. 6-7 replace it.
 //
 // A CTA owns 128 variables and a run of 128-sample tiles.  Each tile is read
-// with coalesced 16-byte loads into shared memory, transposed in 4x4 byte
-// blocks with byte permutes and written out with 16-byte stores.
+// with coalesced 16-byte loads (the next tile's loads are in flight while the
+// current one is transposed), transposed in shared memory in 4x4 byte blocks
+// with byte permutes and written out with 16-byte stores.  A grouped launch
+// covers many datasets: CTA c works for the job whose CTA range holds c.
 #include "internal.cuh"
 
 namespace gbmi {
@@ -49,38 +52,44 @@ __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
     return ((x * 0x01020408u) >> 24) & 0xFu;
 }
 
-template <bool kVec>
-__global__ void __launch_bounds__(kPackThreads)
-pack_kernel(const PackArgs a, const int tiles_per_cta) {
-    __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
-    __shared__ int red[8][kTileJ];
-
+__device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, const int64_t by,
+                                         uint8_t* S, int (*red)[kTileJ]) {
     const int t = threadIdx.x;
     const int w = t >> 5;          // warp: 16-sample slice of the tile
     const int jq = t & 31;         // lane: group of 4 variables
-    const int64_t j0 = static_cast<int64_t>(blockIdx.x) * kTileJ;
-    const int64_t tile_begin = static_cast<int64_t>(blockIdx.y) * tiles_per_cta;
+    const int64_t j0 = bx * kTileJ;
     const int64_t tiles_total = a.ldp / kTileR;
-    const int64_t tile_end = min(tile_begin + tiles_per_cta, tiles_total);
+    const int64_t tile_begin = by * a.tpc;
+    const int64_t tile_end = min(tile_begin + a.tpc, tiles_total);
+    const bool vec = a.vec != 0;
 
     int colsum[4] = {0, 0, 0, 0};
     uint32_t* S32 = reinterpret_cast<uint32_t*>(S);
 
+    // the next tile's 16-byte loads are issued before the current tile is
+    // transposed and stored, so they overlap that work
+    uint4 pre[4];
+    auto load_tile = [&](int64_t tile) {
+        const int64_t r0 = tile * kTileR;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t r = r0 + q * 32 + (t >> 3);
+            const int64_t j = j0 + (t & 7) * 16;
+            pre[q] = make_uint4(0, 0, 0, 0);
+            if (r < a.m && j < a.n)
+                pre[q] = __ldg(reinterpret_cast<const uint4*>(a.X + r * a.ldx + j));
+        }
+    };
+    if (vec && tile_begin < tile_end) load_tile(tile_begin);
+
     for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
         const int64_t r0 = tile * kTileR;
-        // ---- load 128 samples x 128 variables into S[r][j]
-        if (kVec) {
+        // ---- 128 samples x 128 variables into S[r][j]
+        if (vec) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = q * 32 + (t >> 3);
-                const int chunk = t & 7;
-                const int64_t r = r0 + row;
-                const int64_t j = j0 + chunk * 16;
-                uint4 val = make_uint4(0, 0, 0, 0);
-                if (r < a.m && j < a.n)
-                    val = __ldg(reinterpret_cast<const uint4*>(a.X + r * a.ldx + j));
-                *reinterpret_cast<uint4*>(S + row * kTileJ + chunk * 16) = val;
-            }
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(S + (q * 32 + (t >> 3)) * kTileJ + (t & 7) * 16) =
+                    pre[q];
         } else {
             for (int e = t; e < kTileR * kTileJ; e += kPackThreads) {
                 const int row = e / kTileJ;
@@ -91,6 +100,7 @@ pack_kernel(const PackArgs a, const int tiles_per_cta) {
             }
         }
         __syncthreads();
+        if (vec && tile + 1 < tile_end) load_tile(tile + 1);
 
         // ---- transpose: this thread owns samples r0 + 16 w .. +15 of variables 4 jq .. +3
         uint32_t col[4][4];   // col[c][g]: variable 4 jq + c, samples 4 g .. 4 g + 3
@@ -122,7 +132,7 @@ pack_kernel(const PackArgs a, const int tiles_per_cta) {
                 o.y = col[c][1] * 0x38u;
                 o.z = col[c][2] * 0x38u;
                 o.w = col[c][3] * 0x38u;
-                *reinterpret_cast<uint4*>(a.P + j * a.ldp + rbase) = o;
+                *reinterpret_cast<uint4*>(a.P + (tile * a.rows_p + j) * kTileR + w * 16) = o;
             }
             if (a.Bp != nullptr) {
                 const uint32_t bits = bytes_to_nibble(col[c][0]) |
@@ -148,6 +158,29 @@ pack_kernel(const PackArgs a, const int tiles_per_cta) {
     }
 }
 
+__global__ void __launch_bounds__(kPackThreads, 4)   // 4 CTAs per SM: loads in flight
+pack_kernel(const PackJob job) {
+    __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
+    __shared__ int red[8][kTileJ];
+    const int64_t c = blockIdx.x;
+    pack_cta(job, c % job.gx, c / job.gx, S, red);
+}
+
+__global__ void __launch_bounds__(kPackThreads, 4)
+pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs) {
+    __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
+    __shared__ int red[8][kTileJ];
+    const int64_t c = blockIdx.x;
+    int lo = 0, hi = njobs - 1;   // last job whose cta_begin <= c
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].cta_begin <= c) lo = mid; else hi = mid - 1;
+    }
+    const PackJob job = jobs[lo];
+    const int64_t cl = c - job.cta_begin;
+    pack_cta(job, cl % job.gx, cl / job.gx, S, red);
+}
+
 __global__ void validate_kernel(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
                                 unsigned int* flag) {
     const int64_t total = m * n;
@@ -163,20 +196,32 @@ __global__ void validate_kernel(const uint8_t* X, int64_t m, int64_t n, int64_t 
 
 }  // namespace
 
-cudaError_t launch_pack(const PackArgs& a, cudaStream_t s) {
-    if (a.rows_p % kTileJ != 0 || a.ldp % kTileR != 0) return cudaErrorInvalidValue;
+int64_t pack_job_ctas(PackJob& a) {
     const int64_t tiles_total = a.ldp / kTileR;
     int64_t tpc = kTilesPerCta;
-    while ((tiles_total + tpc - 1) / tpc > 65535) tpc *= 2;
-    const int64_t gx = a.rows_p / kTileJ;
-    if (gx > 0x7FFFFFFF) return cudaErrorInvalidValue;
-    dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>((tiles_total + tpc - 1) / tpc));
-    const bool vec = (a.ldx % 16 == 0) && (a.n % 16 == 0) &&
-                     (reinterpret_cast<uintptr_t>(a.X) % 16 == 0);
-    if (vec)
-        pack_kernel<true><<<grid, kPackThreads, 0, s>>>(a, static_cast<int>(tpc));
-    else
-        pack_kernel<false><<<grid, kPackThreads, 0, s>>>(a, static_cast<int>(tpc));
+    a.gx = static_cast<int32_t>(a.rows_p / kTileJ);
+    // keep the job's CTA count moderate for very long sample ranges
+    while ((tiles_total + tpc - 1) / tpc > (int64_t{1} << 16)) tpc *= 2;
+    a.tpc = static_cast<int32_t>(tpc);
+    a.vec = (a.ldx % 16 == 0) && (a.n % 16 == 0) &&
+            (reinterpret_cast<uintptr_t>(a.X) % 16 == 0);
+    return static_cast<int64_t>(a.gx) * ((tiles_total + tpc - 1) / tpc);
+}
+
+cudaError_t launch_pack(const PackJob& job, cudaStream_t s) {
+    if (job.rows_p % kTileJ != 0 || job.ldp % kTileR != 0) return cudaErrorInvalidValue;
+    PackJob j = job;
+    const int64_t ctas = pack_job_ctas(j);
+    if (ctas <= 0 || ctas > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    pack_kernel<<<static_cast<unsigned>(ctas), kPackThreads, 0, s>>>(j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_grouped(const PackJob* jobs, int njobs, int64_t total_ctas,
+                                cudaStream_t s) {
+    if (njobs <= 0 || total_ctas <= 0) return cudaSuccess;
+    if (total_ctas > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    pack_grouped_kernel<<<static_cast<unsigned>(total_ctas), kPackThreads, 0, s>>>(jobs, njobs);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,106 @@
+// Host runtime shared by the C-ABI translation units: per-device workspace,
+// options, the current stream, error text, the launch profiler and counter,
+// the tile-width choice (tuner table or cost model) and TMA descriptors.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gbmi.h"
+#include "internal.cuh"
+
+namespace gbmi {
+namespace rt {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct Options {
+    int fixup = 0;                       // FP64 combine off: the FP32 h-form has no cancellation
+    uint64_t timeout_ns = 2000000000ull;
+    int debug_flags = 0;
+    int group_cols = 8;
+    int max_ctas = 0;
+    int tile_n = 0;                      // 0: tuner table / cost model; else forced 64/128/256
+};
+
+struct DeviceCtx {
+    bool ready = false;
+    int sm_count = 0;
+    DevBuf P, Ba, Bb, va, vb, ha, hb, counts, T, err, tiles, Xs, Ys, outs, flag;
+    int64_t T_len = 0;
+    // tile-list cache of the single-dataset path
+    int64_t tl_na = -1, tl_nb = -1;
+    int tl_sym = -1, tl_group = -1, tl_bn = -1;
+    std::vector<GramTile> tl_host;
+};
+
+extern std::recursive_mutex g_mu;
+extern Options g_opt;
+extern cudaStream_t g_stream;
+extern std::atomic<uint64_t> g_launches;
+
+gbmi_status fail(gbmi_status s, const std::string& msg);
+gbmi_status cuda_fail(cudaError_t e, const char* what);
+gbmi_status ensure(DevBuf& b, size_t bytes, const char* what);
+void release(DevBuf& b);
+gbmi_status get_ctx(DeviceCtx** out);
+DeviceCtx* ctx_of(int dev);
+
+// profiler hooks around each kernel launch (active with GBMI_OPT_PROFILE)
+cudaEvent_t prof_begin(cudaStream_t s);
+void prof_end(const char* name, cudaEvent_t a, cudaStream_t s);
+void prof_set(bool on);
+void prof_collect();
+int prof_entries();
+const char* prof_name(int k);
+double prof_ms(int k);
+int64_t prof_launches(int k);
+void prof_reset();
+
+// MI parameters of m samples (allocates / extends the n log n table when the
+// FP64 combine is on).
+gbmi_status mi_params(DeviceCtx& c, int64_t m, MiParams* P);
+MiParams mi_params_plain(int64_t m, int fixup, const double* T);
+
+// Tile width (B rows per tile, 64/128/256) for a problem: GBMI_OPT_TILE_N if
+// set, else a tuner-table entry for (m, n), else the operand-traffic cost model.
+int choose_bn(int64_t m, int64_t n_a, int64_t n_b, bool symmetric);
+void tuner_set(int64_t m, int64_t n, int bn);
+void tuner_clear();
+int tuner_size();
+
+int grid_for(const DeviceCtx& c, int64_t tiles);
+
+}  // namespace rt
+}  // namespace gbmi
+
+#define GBMI_CUDA(call, what)                                         \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::gbmi::rt::cuda_fail(e_, (what)); \
+    } while (0)
+
+#define GBMI_LAUNCH_ON(stream, call, what)                            \
+    do {                                                              \
+        cudaEvent_t ev0_ = ::gbmi::rt::prof_begin(stream);            \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::gbmi::rt::cuda_fail(e_, (what)); \
+        ::gbmi::rt::prof_end((what), ev0_, stream);                   \
+        ::gbmi::rt::g_launches.fetch_add(1, std::memory_order_relaxed); \
+    } while (0)
+
+#define GBMI_LAUNCH(call, what) GBMI_LAUNCH_ON(::gbmi::rt::g_stream, call, what)
+
+#define GBMI_TRY(expr)                       \
+    do {                                     \
+        gbmi_status s_ = (expr);             \
+        if (s_ != GBMI_OK) return s_;        \
+    } while (0)

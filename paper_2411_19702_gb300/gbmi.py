@@ -19,7 +19,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "gbmi.h")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_BINARY, ERR_UNSUPPORTED = range(7)
 PATH_AUTO, PATH_FUSED, PATH_PLAIN, PATH_POPCOUNT = range(4)
-OPT_FIXUP, OPT_TIMEOUT_NS, OPT_DEBUG_FLAGS, OPT_GROUP_COLS, OPT_MAX_CTAS, OPT_PROFILE = range(1, 7)
+(OPT_FIXUP, OPT_TIMEOUT_NS, OPT_DEBUG_FLAGS, OPT_GROUP_COLS, OPT_MAX_CTAS, OPT_PROFILE,
+ OPT_TILE_N) = range(1, 8)
 _PATHS = {"auto": PATH_AUTO, "fused": PATH_FUSED, "plain": PATH_PLAIN, "popcount": PATH_POPCOUNT}
 STATUS_NAMES = {OK: "OK", ERR_ARG: "ERR_ARG", ERR_OOM: "ERR_OOM", ERR_CUDA: "ERR_CUDA",
                 ERR_TIMEOUT: "ERR_TIMEOUT", ERR_NOT_BINARY: "ERR_NOT_BINARY",
@@ -74,6 +75,9 @@ def load(path: str | None = None):
             "gbmi_shutdown": [],
             "gbmi_profile_reset": [],
             "mi_all_pairs_noalloc": [vp, i64, i64, vp],
+            "gbmi_tuner_set": [i64, i64, i32],
+            "gbmi_tuner_clear": [],
+            "gbmi_tile_n": [i64, i64],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -271,6 +275,20 @@ def mi_cross_host(X, Y, out=None):
         out = np.empty((n1, n2), dtype=np.float32)
     _check(load().mi_cross_host(Xn.ctypes.data, Yn.ctypes.data, m, n1, n2, out.ctypes.data))
     return out
+
+
+def tuner_set(m: int, n: int, tile_n: int):
+    """Record the tile width for problems in the (m, n) bucket."""
+    _check(load().gbmi_tuner_set(int(m), int(n), int(tile_n)))
+
+
+def tuner_clear():
+    _check(load().gbmi_tuner_clear())
+
+
+def tile_n(m: int, n: int) -> int:
+    """Tile width an all-pairs call of shape (m, n) would use."""
+    return int(load().gbmi_tile_n(int(m), int(n)))
 
 
 def set_option(option: int, value: int):

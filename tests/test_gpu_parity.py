@@ -86,6 +86,31 @@ def test_mi_all_pairs_matches_oracle(path, m, n, fixup):
     assert np.all(got >= 0)
 
 
+@pytest.mark.parametrize("tile_n", [64, 128, 256])
+@pytest.mark.parametrize("m,n", [(1000, 200), (129, 127), (1031, 300), (700, 520), (300, 65)])
+def test_tile_widths(tile_n, m, n):
+    """Every tile width of the tensor-core Gram: exact counts, MI vs oracle,
+    all-pairs and cross."""
+    X = _data(m, n, 16)
+    Y = _data(m, n // 2 + 3, 17)
+    want, n11 = oracle.mi_matrix(X)
+    wantc, n11c = oracle.mi_matrix(X, Y)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    gbmi.set_option(gbmi.OPT_TILE_N, tile_n)
+    try:
+        c = gbmi.counts_all_pairs(Xd, path="plain").cpu().numpy()
+        cc = gbmi.counts_cross(Xd, Yd, path="plain").cpu().numpy()
+        mi = gbmi.mi_all_pairs(Xd, path="fused").cpu().numpy()
+        mic = gbmi.mi_cross(Xd, Yd, path="fused").cpu().numpy()
+        gbmi.sync()
+    finally:
+        gbmi.set_option(gbmi.OPT_TILE_N, 0)
+    assert np.array_equal(c, n11) and np.array_equal(cc, n11c)
+    assert np.max(np.abs(mi.astype(np.float64) - want)) <= MI_TOL
+    assert np.array_equal(mi, mi.T)
+    assert np.max(np.abs(mic.astype(np.float64) - wantc)) <= MI_TOL
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_small_mi_relative_accuracy(path, fixup):
     """Near independence (most pairs of sparse data) the FP32 form has no
