@@ -175,6 +175,47 @@ uint64_t gbmi_launch_count(void);
 /* Free the workspace (waits for the device first). */
 gbmi_status gbmi_shutdown(void);
 
+/* ----------------------------------------------------------------- batches
+ *
+ * Many independent problems (datasets of uneven m and n) in one grouped run
+ * (no counterpart in the paper, which treats one dataset at a time).  Each
+ * job is the paper's all-pairs problem on its own X (Y == NULL) or the cross
+ * problem between X and Y over the same samples.  A plan packs every job's
+ * operands into one workspace and runs, on the library's current stream, a
+ * CUDA graph of four kernels: column counts zeroing, one grouped pack, one
+ * grouped per-variable-terms pass and ONE persistent tensor-core Gram launch
+ * whose tile list holds the tiles of all jobs (largest tiles first; each
+ * job's tile width from the tuner table).  Results are bit-identical to the
+ * single calls (the counts are exact and the per-pair arithmetic is the same).
+ * Limits per job: 1 <= m <= 2^24 (fused path), 1 <= n, n2.  Device pointers
+ * X, Y, out as in mi_all_pairs / mi_cross.
+ *
+ * gbmi_batch_create allocates the plan's workspace, uploads its tables and
+ * captures the graph (call it outside stream capture).  gbmi_batch_run
+ * launches the graph (asynchronous).  gbmi_batch_set_io points the same plan
+ * at new X / Y / out buffers of the same shapes (tables only; the graph is
+ * reused).  gbmi_batch_destroy waits for the device and frees the plan.
+ * gbmi_mi_batch is create + run + wait + destroy.  Device-side timeouts are
+ * reported by gbmi_sync(). */
+typedef struct {
+    const uint8_t* X;   /* m x n samples x variables, uint8 0/1 */
+    const uint8_t* Y;   /* m x n2 for cross MI, or NULL for all pairs of X */
+    int64_t m;
+    int64_t n;
+    int64_t n2;         /* columns of Y; ignored when Y is NULL */
+    float* out;         /* n x n (all pairs) or n x n2 (cross), FP32 bits */
+} gbmi_job;
+
+typedef struct gbmi_batch gbmi_batch;
+
+gbmi_status gbmi_batch_create(const gbmi_job* jobs, int k, gbmi_batch** plan);
+gbmi_status gbmi_batch_run(gbmi_batch* plan);
+gbmi_status gbmi_batch_set_io(gbmi_batch* plan, const gbmi_job* jobs, int k);
+gbmi_status gbmi_batch_destroy(gbmi_batch* plan);
+gbmi_status gbmi_mi_batch(const gbmi_job* jobs, int k);
+/* Number of tensor-core tiles in the plan's grouped launch. */
+int64_t gbmi_batch_tiles(const gbmi_batch* plan);
+
 /* Tile-width table of the autotuner (no counterpart in the paper).  The
  * tensor-core Gram works on tiles of 128 x tile_n variable pairs; narrow tiles
  * waste less padding on small n, wide tiles stream fewer operand bytes per

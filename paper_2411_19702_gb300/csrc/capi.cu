@@ -107,6 +107,8 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     L.err = static_cast<unsigned int*>(c.err.p);
     L.timeout_ns = g_opt.timeout_ns;
     L.debug_flags = g_opt.debug_flags;
+    GBMI_TRY(ensure(c.sched, 256, "tile counter"));
+    L.counter = static_cast<unsigned int*>(c.sched.p);
     const int64_t kb_total = pack_ld(m) / kTcBK;
     const int64_t kb_chunk = kExactChunk / kTcBK;
     if (mode == kTcModeMI && kb_total > kb_chunk)
@@ -116,6 +118,7 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
         L.job0.k_begin = static_cast<int32_t>(k0);
         L.job0.k_blocks = static_cast<int32_t>(std::min(kb_chunk, kb_total - k0));
         L.mode = (mode == kTcModeMI) ? kTcModeMI : (k0 == 0 ? kTcModeCounts : kTcModeCountsAdd);
+        GBMI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
         GBMI_LAUNCH(launch_gram_tc(maps, L, grid, g_stream),
                     L.mode == kTcModeMI ? "gram_tc_fused_mi" : "gram_tc_counts");
     }
@@ -538,6 +541,7 @@ gbmi_status gbmi_shutdown(void) {
         if (c == nullptr || !c->ready) continue;
         cudaSetDevice(d);
         cudaDeviceSynchronize();
+        rt::release(c->sched);
         for (DevBuf* b : {&c->P, &c->Ba, &c->Bb, &c->va, &c->vb, &c->ha, &c->hb, &c->counts,
                           &c->T, &c->err, &c->tiles, &c->Xs, &c->Ys, &c->outs, &c->flag})
             rt::release(*b);

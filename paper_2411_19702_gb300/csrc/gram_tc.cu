@@ -29,8 +29,13 @@
 //               (j, i) as coalesced rows.  The second accumulator lets tile
 //               t+1's MMAs run meanwhile.
 // Tiles come from a host-built list: for all-pairs only blocks that touch
-// the upper triangle (j >= i), in groups of column blocks so that CTAs running
-// at the same time share operand panels in L2.
+// the upper triangle (j >= i), in groups of column blocks, jobs one after
+// another, so that CTAs running at the same time share operand panels in L2.
+// The producer takes the CTA's next tile from a shared atomic counter
+// (dynamic order: the tiles in flight are always a contiguous window of the
+// list, whatever their lengths) or from the static round-robin sequence, and
+// hands its id to the MMA thread and the epilogue warps through an 8-entry
+// shared-memory queue (queue full / queue empty mbarriers; -1 ends the run).
 //
 // Every mbarrier wait is bounded (timeout_ns from its start, %globaltimer).
 // A role whose wait runs out sets a bit in the device error word and a
@@ -61,10 +66,13 @@ constexpr int kGroup = 16;                       // accumulator columns per tcge
 constexpr size_t kOffStages = 0;
 constexpr size_t kOffColVars = kOffStages + static_cast<size_t>(kStages) * kStageBytes;
 constexpr size_t kColVarBytes = static_cast<size_t>(kColsPerWarpMax) * sizeof(MiVar);   // 4 KB
+constexpr int kQ = 8;                            // tile-id queue between the roles
 constexpr size_t kOffBars = kOffColVars + kEpiWarps * kColVarBytes;
-constexpr int kNumBars = 2 * kStages + 4 + 1;    // full, empty, tmem full x2, tmem empty x2, drain
+// full, empty, tmem full x2, tmem empty x2, drain, queue full x kQ, queue empty x kQ
+constexpr int kNumBars = 2 * kStages + 4 + 1 + 2 * kQ;
 constexpr size_t kOffMisc = kOffBars + kNumBars * 8;
-constexpr size_t kSmemBytes = 1024 + kOffMisc + 64;
+constexpr size_t kOffQueue = kOffMisc + 64;
+constexpr size_t kSmemBytes = 1024 + kOffQueue + kQ * 4;
 
 static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte alignment");
 static_assert(kSmemBytes <= 232448, "shared memory budget");
@@ -82,6 +90,13 @@ struct Smem {
     __device__ uint32_t tfull(int b) const { return ptx::smem_u32(bar(2 * kStages + b)); }
     __device__ uint32_t tempty(int b) const { return ptx::smem_u32(bar(2 * kStages + 2 + b)); }
     __device__ uint32_t drain() const { return ptx::smem_u32(bar(2 * kStages + 4)); }
+    __device__ uint32_t qfull(int q) const { return ptx::smem_u32(bar(2 * kStages + 5 + q)); }
+    __device__ uint32_t qempty(int q) const {
+        return ptx::smem_u32(bar(2 * kStages + 5 + kQ + q));
+    }
+    __device__ volatile int* queue() const {
+        return reinterpret_cast<volatile int*>(base + kOffQueue);
+    }
     __device__ uint32_t* tmem_holder() const {
         return reinterpret_cast<uint32_t*>(base + kOffMisc);
     }
@@ -100,16 +115,43 @@ __device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
 }
 
 // ------------------------------------------------------------------ producer
+// Next tile of this CTA: from the shared counter (dynamic order) or the static
+// round-robin sequence.
+__device__ __forceinline__ int next_tile(const GramLaunch& L, int s) {
+    if (L.counter != nullptr) return static_cast<int>(atomicAdd(L.counter, 1u));
+    return blockIdx.x + s * gridDim.x;
+}
+
 __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const GramLaunch& L) {
     int pending_parity[kStages];
 #pragma unroll
     for (int s = 0; s < kStages; ++s) pending_parity[s] = -1;
-    if (L.debug_flags & 1) return;   // test hook: issue nothing, consumers must time out
     int stage = 0;
     uint32_t phase = 0;
+    int qslot = 0;
+    uint32_t qphase = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < L.num_tiles && ok; t += gridDim.x) {
-        const GramTile tile = L.tiles[t];
+    int s = 0;
+    int t = next_tile(L, 0);
+    while (ok) {
+        // publish the tile id (-1 at the end) to the MMA thread and the epilogue
+        if (!ptx::mbar_wait_bounded(sm.qempty(qslot), qphase ^ 1u, L.timeout_ns,
+                                    sm.abort_flag())) {
+            raise_abort(sm, L.err, kErrTimeoutLoad);
+            ok = false;
+            break;
+        }
+        const int tid = t < L.num_tiles ? t : -1;
+        sm.queue()[qslot] = tid;
+        ptx::mbar_arrive(sm.qfull(qslot));
+        if (++qslot == kQ) {
+            qslot = 0;
+            qphase ^= 1u;
+        }
+        if (tid < 0) break;
+        if (L.debug_flags & 1) break;   // test hook: issue no copies, consumers must time out
+        const int t_next = next_tile(L, ++s);   // its latency overlaps this tile's copies
+        const GramTile tile = L.tiles[tid];
         const GramJob& job = job_of(L, tile.job);
         const int bn = job.bn;
         const CUtensorMap* mapB = bn == 256 ? &maps.box256 : (bn == 128 ? &maps.box128
@@ -136,14 +178,15 @@ __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const Gram
                 phase ^= 1u;
             }
         }
+        t = t_next;
     }
     if (!ok || *sm.abort_flag()) {
         // Unwinding: wait (bounded) until every copy this thread issued has landed.
         const uint64_t d2 = ptx::globaltimer_ns() + 100000000ull;
-        for (int s = 0; s < kStages; ++s) {
-            if (pending_parity[s] < 0) continue;
-            const uint32_t bar = sm.full(s);
-            const uint32_t par = static_cast<uint32_t>(pending_parity[s]);
+        for (int s2 = 0; s2 < kStages; ++s2) {
+            if (pending_parity[s2] < 0) continue;
+            const uint32_t bar = sm.full(s2);
+            const uint32_t par = static_cast<uint32_t>(pending_parity[s2]);
             while (!ptx::mbar_try_wait(bar, par)) {
                 if (ptx::globaltimer_ns() > d2) {
                     atomicOr(L.err, kErrTimeoutDrain);
@@ -160,8 +203,21 @@ __device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base)
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
+    int qslot = 0;
+    uint32_t qphase = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < L.num_tiles && ok; t += gridDim.x) {
+    while (ok) {
+        if (!ptx::mbar_wait_bounded(sm.qfull(qslot), qphase, L.timeout_ns, sm.abort_flag())) {
+            raise_abort(sm, L.err, kErrTimeoutMma);
+            break;
+        }
+        const int t = sm.queue()[qslot];
+        ptx::mbar_arrive(sm.qempty(qslot));
+        if (++qslot == kQ) {
+            qslot = 0;
+            qphase ^= 1u;
+        }
+        if (t < 0) break;
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
         const uint32_t idesc = ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(job.bn));
@@ -235,7 +291,21 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
     MiVar* cv = sm.colvars(warp - 2);                  // this warp's column terms
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < L.num_tiles; t += gridDim.x) {
+    int qslot = 0;
+    uint32_t qphase = 0;
+    for (;;) {
+        if (!ptx::mbar_wait_bounded(sm.qfull(qslot), qphase, L.timeout_ns, sm.abort_flag())) {
+            raise_abort(sm, L.err, kErrTimeoutEpilogue);
+            break;
+        }
+        const int t = sm.queue()[qslot];
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(sm.qempty(qslot));
+        if (++qslot == kQ) {
+            qslot = 0;
+            qphase ^= 1u;
+        }
+        if (t < 0) break;
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
         const MiParams& P = job.mp;
@@ -419,6 +489,10 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
             ptx::mbar_init(sm.tempty(b), kEpiWarps * 32);
         }
         ptx::mbar_init(sm.drain(), 1);
+        for (int q = 0; q < kQ; ++q) {
+            ptx::mbar_init(sm.qfull(q), 1);
+            ptx::mbar_init(sm.qempty(q), 1 + kEpiWarps);   // MMA thread + one lane per warp
+        }
         *sm.abort_flag() = 0;
         ptx::fence_barrier_init();
     }

@@ -131,6 +131,10 @@ struct GramLaunch {
     unsigned int* err;
     uint64_t timeout_ns;
     int debug_flags;
+    // Dynamic tile order: CTAs take the next tile from this counter (zero at
+    // launch), so the tiles in flight are always a contiguous window of the
+    // list.  Null: static round-robin (tile blockIdx.x + k * gridDim.x).
+    unsigned int* counter;
 };
 
 // TMA descriptors of a K-block-major operand buffer of total_rows rows of 128

@@ -47,6 +47,38 @@ __device__ __forceinline__ void transpose4x4(const uint32_t w0, const uint32_t w
     c3 = __byte_perm(t2, t3, 0x7632);
 }
 
+// 16 bytes starting at any address p, of which the first nvalid (1..16) are
+// kept and the rest zeroed.  Only the 16-byte-aligned granules that hold the
+// bytes [p, p + nvalid) are read, so nothing outside the caller's range is
+// touched, and the bytes are shifted into place with funnel shifts.
+__device__ __forceinline__ uint4 load16_any(const uint8_t* p, int nvalid) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const int s = static_cast<int>(a & 15);
+    const uint4* g = reinterpret_cast<const uint4*>(a - s);
+    const uint4 g0 = __ldg(g);
+    uint4 g1 = make_uint4(0, 0, 0, 0);
+    if (s + nvalid > 16) g1 = __ldg(g + 1);
+    const uint32_t w[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    const int q = s >> 2;
+    const uint32_t sh = static_cast<uint32_t>(s & 3) * 8u;
+    uint32_t sel[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        sel[i] = q == 0 ? w[i] : (q == 1 ? w[i + 1] : (q == 2 ? w[i + 2] : w[i + 3]));
+    uint32_t o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        o[i] = __funnelshift_r(sel[i], sel[i + 1], sh);
+        const int keep = nvalid - 4 * i;   // bytes of this word that are valid
+        if (keep <= 0) {
+            o[i] = 0u;
+        } else if (keep < 4) {
+            o[i] &= (1u << (8 * keep)) - 1u;
+        }
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
 // Low bits of the four 0/1 bytes of x, packed into a nibble (byte k -> bit k).
 __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
     return ((x * 0x01020408u) >> 24) & 0xFu;
@@ -68,6 +100,7 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
 
     // the next tile's 16-byte loads are issued before the current tile is
     // transposed and stored, so they overlap that work
+    // (rows of X that are not 16-byte aligned go through load16_any)
     uint4 pre[4];
     auto load_tile = [&](int64_t tile) {
         const int64_t r0 = tile * kTileR;
@@ -76,31 +109,25 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
             const int64_t r = r0 + q * 32 + (t >> 3);
             const int64_t j = j0 + (t & 7) * 16;
             pre[q] = make_uint4(0, 0, 0, 0);
-            if (r < a.m && j < a.n)
-                pre[q] = __ldg(reinterpret_cast<const uint4*>(a.X + r * a.ldx + j));
+            if (r < a.m && j < a.n) {
+                const uint8_t* p = a.X + r * a.ldx + j;
+                if (vec)
+                    pre[q] = __ldg(reinterpret_cast<const uint4*>(p));
+                else
+                    pre[q] = load16_any(p, a.n - j < 16 ? static_cast<int>(a.n - j) : 16);
+            }
         }
     };
-    if (vec && tile_begin < tile_end) load_tile(tile_begin);
+    if (tile_begin < tile_end) load_tile(tile_begin);
 
     for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
         const int64_t r0 = tile * kTileR;
         // ---- 128 samples x 128 variables into S[r][j]
-        if (vec) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(S + (q * 32 + (t >> 3)) * kTileJ + (t & 7) * 16) =
-                    pre[q];
-        } else {
-            for (int e = t; e < kTileR * kTileJ; e += kPackThreads) {
-                const int row = e / kTileJ;
-                const int col = e % kTileJ;
-                const int64_t r = r0 + row;
-                const int64_t j = j0 + col;
-                S[e] = (r < a.m && j < a.n) ? __ldg(a.X + r * a.ldx + j) : 0;
-            }
-        }
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(S + (q * 32 + (t >> 3)) * kTileJ + (t & 7) * 16) = pre[q];
         __syncthreads();
-        if (vec && tile + 1 < tile_end) load_tile(tile + 1);
+        if (tile + 1 < tile_end) load_tile(tile + 1);
 
         // ---- transpose: this thread owns samples r0 + 16 w .. +15 of variables 4 jq .. +3
         uint32_t col[4][4];   // col[c][g]: variable 4 jq + c, samples 4 g .. 4 g + 3

@@ -35,6 +35,7 @@ struct DeviceCtx {
     bool ready = false;
     int sm_count = 0;
     DevBuf P, Ba, Bb, va, vb, ha, hb, counts, T, err, tiles, Xs, Ys, outs, flag;
+    DevBuf sched;   // tile counter of the Gram launches (zeroed before each launch)
     int64_t T_len = 0;
     // tile-list cache of the single-dataset path
     int64_t tl_na = -1, tl_nb = -1;

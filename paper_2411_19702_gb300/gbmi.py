@@ -78,6 +78,11 @@ def load(path: str | None = None):
             "gbmi_tuner_set": [i64, i64, i32],
             "gbmi_tuner_clear": [],
             "gbmi_tile_n": [i64, i64],
+            "gbmi_batch_create": [vp, i32, vp],
+            "gbmi_batch_run": [vp],
+            "gbmi_batch_set_io": [vp, vp, i32],
+            "gbmi_batch_destroy": [vp],
+            "gbmi_mi_batch": [vp, i32],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -99,6 +104,8 @@ def load(path: str | None = None):
         lib.gbmi_profile_ms.restype = ctypes.c_double
         lib.gbmi_profile_launches.argtypes = [ctypes.c_int]
         lib.gbmi_profile_launches.restype = ctypes.c_int64
+        lib.gbmi_batch_tiles.argtypes = [vp]
+        lib.gbmi_batch_tiles.restype = ctypes.c_int64
         _lib = lib
         return lib
 
@@ -275,6 +282,98 @@ def mi_cross_host(X, Y, out=None):
         out = np.empty((n1, n2), dtype=np.float32)
     _check(load().mi_cross_host(Xn.ctypes.data, Yn.ctypes.data, m, n1, n2, out.ctypes.data))
     return out
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("n2", ctypes.c_int64), ("out", ctypes.c_void_p)]
+
+
+def _jobs(Xs, Ys, outs):
+    import torch
+    Ys = list(Ys) if Ys is not None else [None] * len(Xs)
+    if len(Ys) != len(Xs):
+        raise ValueError("Ys must match Xs")
+    arr = (_Job * len(Xs))()
+    keep, out_list = [], []
+    for k, X in enumerate(Xs):
+        X = _prep(X)
+        Y = None if Ys[k] is None else _prep(Ys[k], "Y")
+        m, n = X.shape
+        n2 = n if Y is None else Y.shape[1]
+        if Y is not None and Y.shape[0] != m:
+            raise ValueError(f"job {k}: X and Y must have the same number of samples")
+        o = None if outs is None else outs[k]
+        if o is None:
+            o = torch.empty((n, n2), dtype=torch.float32, device=X.device)
+        if o.shape != (n, n2) or o.dtype != torch.float32 or not o.is_contiguous():
+            raise ValueError(f"job {k}: out must be a contiguous float32 ({n}, {n2}) tensor")
+        arr[k] = _Job(X.data_ptr(), 0 if Y is None else Y.data_ptr(), m, n, n2 if Y is not None
+                      else 0, o.data_ptr())
+        keep += [X, Y]
+        out_list.append(o)
+    return arr, keep, out_list
+
+
+class Batch:
+    """A plan for many all-pairs (Y=None) or cross problems in one grouped run.
+
+    ``run()`` launches the plan's CUDA graph (one grouped pack, one grouped
+    per-variable pass and one persistent tensor-core Gram launch over the tiles
+    of every job) on the current stream; ``outs`` are the output tensors.
+    """
+
+    def __init__(self, Xs, Ys=None, outs=None):
+        import torch
+        self._dev = _prep(Xs[0]).device
+        arr, self._keep, self.outs = _jobs(Xs, Ys, outs)
+        self._plan = ctypes.c_void_p()
+        with torch.cuda.device(self._dev):
+            lib = _bind_stream(self._dev)
+            _check(lib.gbmi_batch_create(arr, len(Xs), ctypes.byref(self._plan)))
+
+    @property
+    def tiles(self) -> int:
+        return int(load().gbmi_batch_tiles(self._plan))
+
+    def run(self):
+        import torch
+        with torch.cuda.device(self._dev):
+            lib = _bind_stream(self._dev)
+            _check(lib.gbmi_batch_run(self._plan))
+        return self.outs
+
+    def set_io(self, Xs, Ys=None, outs=None):
+        import torch
+        arr, keep, out_list = _jobs(Xs, Ys, outs)
+        with torch.cuda.device(self._dev):
+            lib = _bind_stream(self._dev)
+            _check(lib.gbmi_batch_set_io(self._plan, arr, len(Xs)))
+        self._keep, self.outs = keep, out_list
+        return self.outs
+
+    def close(self):
+        if self._plan:
+            _check(load().gbmi_batch_destroy(self._plan))
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mi_batch(Xs, Ys=None, outs=None):
+    """One-shot grouped run (create, run, wait, destroy); returns the outputs."""
+    import torch
+    arr, keep, out_list = _jobs(Xs, Ys, outs)
+    dev = out_list[0].device
+    with torch.cuda.device(dev):
+        lib = _bind_stream(dev)
+        _check(lib.gbmi_mi_batch(arr, len(Xs)))
+    del keep
+    return out_list
 
 
 def tuner_set(m: int, n: int, tile_n: int):

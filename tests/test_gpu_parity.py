@@ -124,6 +124,24 @@ def test_small_mi_relative_accuracy(path, fixup):
     assert rel.max() <= 1e-4, rel.max()
 
 
+@pytest.mark.parametrize("offset", [1, 3, 8, 13])
+@pytest.mark.parametrize("m,n", [(300, 200), (257, 131), (1000, 64)])
+def test_unaligned_input_base(offset, m, n):
+    """X starting at any byte address (a view into a larger buffer)."""
+    X = _data(m, n, 18)
+    buf = torch.zeros(m * n + 64, dtype=torch.uint8, device="cuda")
+    buf[offset:offset + m * n] = torch.from_numpy(X.reshape(-1)).cuda()
+    Xv = buf[offset:offset + m * n].view(m, n)
+    assert Xv.data_ptr() % 16 == offset % 16
+    want, n11 = oracle.mi_matrix(X)
+    v = gbmi.column_counts(Xv).cpu().numpy()
+    c = gbmi.counts_all_pairs(Xv, path="plain").cpu().numpy()
+    mi = gbmi.mi_all_pairs(Xv, path="fused").cpu().numpy()
+    gbmi.sync()
+    assert np.array_equal(v, X.sum(axis=0)) and np.array_equal(c, n11)
+    assert np.max(np.abs(mi.astype(np.float64) - want)) <= MI_TOL
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_mi_cross_matches_oracle(path, fixup):
     X, Y = _data(1500, 290, 6), _data(1500, 77, 7)

@@ -1,0 +1,69 @@
+"""Tile-width tuner table and the batch API's argument checks, without a GPU."""
+from __future__ import annotations
+
+import ctypes
+
+import pytest
+
+from paper_2411_19702_gb300 import autotune
+from paper_2411_19702_gb300 import build as gbuild
+from paper_2411_19702_gb300 import gbmi
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    gbmi.load(gbuild.build())
+    yield
+    gbmi.tuner_clear()
+
+
+def test_cost_model_prefers_wide_tiles_for_large_n_and_narrow_for_tiny_n():
+    gbmi.tuner_clear()
+    assert gbmi.tile_n(100_000, 10_000) == 256
+    assert gbmi.tile_n(5_000, 64) == 64
+
+
+def test_tuner_entries_cover_their_bucket_only():
+    gbmi.tuner_clear()
+    before = gbmi.tile_n(100_000, 10_000)
+    gbmi.tuner_set(100_000, 10_000, 128)
+    # same bucket: floor(log2 m) = 16, floor(2 log2 n) = 26
+    assert gbmi.tile_n(70_000, 10_500) == 128
+    assert gbmi.tile_n(100_000, 10_000) == 128
+    # other buckets keep the model's choice
+    assert gbmi.tile_n(300_000, 10_000) == before
+    assert gbmi.tile_n(100_000, 20_000) == gbmi.tile_n(100_000, 20_000)
+    gbmi.tuner_clear()
+    assert gbmi.tile_n(100_000, 10_000) == before
+
+
+def test_tuner_rejects_bad_widths():
+    with pytest.raises(gbmi.GbmiError):
+        gbmi.tuner_set(1000, 100, 96)
+    with pytest.raises(gbmi.GbmiError):
+        gbmi.set_option(gbmi.OPT_TILE_N, 100)
+
+
+def test_autotune_table_round_trip(tmp_path):
+    table = {"16,26": {"m": 100_000, "n": 10_000, "tile_n": 128,
+                       "ms": {"64": 3.0, "128": 2.0, "256": 2.5}}}
+    path = str(tmp_path / "tune.json")
+    autotune.save(table, path)
+    gbmi.tuner_clear()
+    got = autotune.load(path)
+    assert got == table
+    assert gbmi.tile_n(100_000, 10_000) == 128
+    assert autotune.bucket(100_000, 10_000) == (16, 26)
+    gbmi.tuner_clear()
+
+
+def test_batch_argument_errors_need_no_gpu():
+    lib = gbmi.load()
+    plan = ctypes.c_void_p()
+    assert lib.gbmi_batch_create(None, 0, ctypes.byref(plan)) == gbmi.ERR_ARG
+    jobs = (gbmi._Job * 1)()
+    jobs[0] = gbmi._Job(0, 0, 10, 4, 0, 0)          # null X and out
+    assert lib.gbmi_batch_create(jobs, 1, ctypes.byref(plan)) == gbmi.ERR_ARG
+    jobs[0] = gbmi._Job(16, 0, (1 << 24) + 1, 4, 0, 32)   # m beyond the fused limit
+    assert lib.gbmi_batch_create(jobs, 1, ctypes.byref(plan)) == gbmi.ERR_ARG
+    assert b"2^24" in lib.gbmi_last_error_string()
