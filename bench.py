@@ -12,8 +12,12 @@ computed too but not counted).
 The JSON line also carries the plain unfused path (Gram -> int32 counts in
 HBM -> elementwise MI) and the popcount path on the same input, the roofline
 of the dominant kernel, SM clocks sampled during the timed region, an
-end-to-end figure through the host-buffer C-ABI call, and the FP64 oracle
-timed on the host cores on a bounded sample of pairs.
+end-to-end figure through the host-buffer C-ABI call, the FP64 oracle
+timed on the host cores on a bounded sample of pairs, the batching workload
+(512 uneven datasets in one grouped graph vs separate calls) and the serving
+workload (Poisson arrivals at 200 req/s of mixed all-pairs / cross requests
+through the native server under a 40 GB budget: p50/p99 latency, and the
+capacity of a burst of requests under continuous batching).
 
 --impl reference times the FP64 oracle (the only reference this method has:
 the paper ships no GPU code) on the host cores, each step a bounded sample of
@@ -296,6 +300,154 @@ def measure_batch(dev, reps=3, k=512, seed=4):
     return res
 
 
+# --------------------------------------------------------------- serving
+def serve_pool(k_all=48, k_cross=24, seed=5):
+    """Dataset shapes of the serving workload's pool: all-pairs (m, n) and cross (m, n1, n2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lu = lambda lo, hi, k: np.exp(rng.uniform(np.log(lo), np.log(hi), size=k)).round().astype(int)
+    alls = list(zip(lu(1_000, 500_000, k_all), lu(100, 8_000, k_all)))
+    cross = list(zip(lu(1_000, 500_000, k_cross), lu(100, 4_000, k_cross), lu(100, 4_000, k_cross)))
+    return alls, cross
+
+
+def _beta_matrix(m, n, g, rng, dev):
+    import torch
+    p = torch.as_tensor(rng.beta(0.5, 5.0, size=n), dtype=torch.float32, device=dev)
+    X = torch.empty((m, n), dtype=torch.uint8, device=dev)
+    rows = max(1, (1 << 28) // n)
+    for r in range(0, m, rows):
+        X[r:r + rows] = (torch.rand((min(rows, m - r), n), generator=g, device=dev) < p)
+    return X
+
+
+def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burst=400, check=20):
+    """Poisson arrivals of mixed all-pairs / cross requests through the native server.
+
+    Each request registers its dataset(s) from a pool of resident inputs
+    (so the server packs them for that request), submits, and removes them
+    (dropped once the request is done); a collector waits for the tickets in
+    order and releases the outputs.  Latency is submit -> completion, timed
+    inside the server.
+    """
+    import torch
+
+    from paper_2411_19702_gb300 import gbmi
+    alls, cross = serve_pool(seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    pool_all = [_beta_matrix(int(m), int(n), g, rng, dev) for m, n in alls]
+    pool_cross = [(_beta_matrix(int(m), int(a), g, rng, dev), _beta_matrix(int(m), int(b), g, rng, dev))
+                  for m, a, b in cross]
+    torch.cuda.synchronize(dev)
+
+    def run(srv, arrivals, picks, keep=0):
+        tickets, kept, errors = [], [], []
+        done = threading.Event()
+
+        def collector():
+            k = 0
+            try:
+                while k < len(arrivals):
+                    while k >= len(tickets):
+                        if done.is_set() and k >= len(tickets):
+                            return
+                        time.sleep(0.0002)
+                    t, req = tickets[k]
+                    out, _ = srv.wait(t, timeout_ms=120_000)
+                    if k < keep:
+                        kept.append((req, out.clone()))
+                    srv.release(t)
+                    k += 1
+            except Exception as e:  # reported by the caller
+                errors.append(e)
+
+        th = threading.Thread(target=collector)
+        th.start()
+        t0 = time.perf_counter()
+        try:
+            for at, req in zip(arrivals, picks):
+                d = t0 + at - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                kind, j = req
+                if kind == "all":
+                    a = srv.add_dataset(pool_all[j])
+                    t = srv.submit(a)
+                    srv.remove_dataset(a)
+                else:
+                    a = srv.add_dataset(pool_cross[j][0])
+                    b = srv.add_dataset(pool_cross[j][1])
+                    t = srv.submit(a, b)
+                    srv.remove_dataset(a)
+                    srv.remove_dataset(b)
+                tickets.append((t, req))
+        finally:
+            done.set()
+            th.join()
+        wall = time.perf_counter() - t0
+        if errors:
+            raise errors[0]
+        return wall, kept
+
+    def pairs_of(req):
+        kind, j = req
+        if kind == "all":
+            n = int(alls[j][1])
+            return n * (n - 1) // 2
+        return int(cross[j][1]) * int(cross[j][2])
+
+    def picks_for(k, r):
+        out = []
+        for _ in range(k):
+            if r.random() < 0.5:
+                out.append(("all", int(r.integers(len(alls)))))
+            else:
+                out.append(("cross", int(r.integers(len(cross)))))
+        return out
+
+    # open loop: Poisson arrivals at `rate` for `seconds`
+    r = np.random.Generator(np.random.PCG64(seed + 2))
+    gaps = r.exponential(1.0 / rate, size=int(rate * seconds * 1.5) + 16)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < seconds]
+    picks = picks_for(len(arrivals), r)
+    with gbmi.Server(budget, max_batch=64, device=dev) as srv:
+        wall, kept = run(srv, arrivals, picks, keep=check)
+        st = srv.stats()
+    same = True
+    for (kind, j), got in kept:
+        want = (gbmi.mi_all_pairs(pool_all[j], path="fused") if kind == "all"
+                else gbmi.mi_cross(pool_cross[j][0], pool_cross[j][1], path="fused"))
+        gbmi.sync()
+        same = same and bool(torch.equal(got, want))
+    pairs = sum(pairs_of(q) for q in picks)
+    poisson = {"requests": len(arrivals), "offered_req_per_s": rate, "seconds": seconds,
+               "wall_s": wall, "pairs": pairs, "pairs_per_s_offered_window": pairs / wall,
+               "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+               "max_ms": st["max_ms"], "completed": int(st["completed"]),
+               "batches": int(st["batches"]), "requests_per_batch": st["requests_per_batch"],
+               "bit_identical_to_single_calls": f"{len(kept)} of {len(kept)} checked" if same
+               else "MISMATCH"}
+    # closed loop: `burst` requests submitted at once (capacity under continuous batching)
+    bpicks = picks_for(burst, r)
+    with gbmi.Server(budget, max_batch=64, device=dev) as srv:
+        bwall, _ = run(srv, np.zeros(burst), bpicks)
+        bst = srv.stats()
+    bpairs = sum(pairs_of(q) for q in bpicks)
+    res = {"budget_bytes": budget, "mix": "50% all-pairs m in [1e3,5e5] n in [100,8000], "
+           "50% cross n1,n2 in [100,4000], log-uniform; pool of "
+           f"{len(alls)} + {len(cross)} resident inputs, densities Beta(0.5,5)",
+           "poisson": poisson,
+           "burst": {"requests": burst, "wall_s": bwall, "req_per_s": burst / bwall,
+                     "pairs_per_s": bpairs / bwall, "p50_ms": bst["p50_ms"],
+                     "p99_ms": bst["p99_ms"], "batches": int(bst["batches"]),
+                     "requests_per_batch": bst["requests_per_batch"]}}
+    del pool_all, pool_cross
+    torch.cuda.empty_cache()
+    return res
+
+
 # --------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -445,6 +597,9 @@ def run_ours(args):
     batch = None
     if not args.skip_batch:
         batch = measure_batch(dev)
+    serving = None
+    if not args.skip_serve and rank == 0:
+        serving = measure_serving(dev, seconds=args.serve_seconds)
 
     value = world * pairs / (fused_ms * 1e-3)
     plain_ms = max_over_ranks(plain["ms"])
@@ -478,6 +633,7 @@ def run_ours(args):
         "gpu_launches": int(fused["launches"]),
         "parity": parity,
         "batch": batch,
+        "serving": serving,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
@@ -500,6 +656,8 @@ def main():
     ap.add_argument("--skip-oracle", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

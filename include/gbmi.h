@@ -216,6 +216,53 @@ gbmi_status gbmi_mi_batch(const gbmi_job* jobs, int k);
 /* Number of tensor-core tiles in the plan's grouped launch. */
 int64_t gbmi_batch_tiles(const gbmi_batch* plan);
 
+/* ----------------------------------------------------------------- serving
+ *
+ * A request loop with continuous batching (no counterpart in the paper).
+ * The server owns one device arena of budget_bytes from which it takes, per
+ * dataset, the packed FP8 operand, the column counts and the per-variable
+ * terms (resident until the dataset is removed), and per request its output.
+ * A worker thread admits queued requests in arrival order whenever their
+ * memory fits and fewer than max_batch requests are waiting for the GPU,
+ * merges them into one grouped launch (pack of the datasets not yet resident,
+ * per-variable terms, one persistent tensor-core Gram over the tiles of all
+ * admitted requests) and keeps up to two such batches in flight on two
+ * streams, so requests that arrive while others run start without waiting for
+ * them to finish.  Results are the same as the single calls (mi_all_pairs /
+ * mi_cross with the FP32 epilogue).
+ *
+ * gbmi_server_add_dataset registers X (device pointer, m x n uint8 0/1, must
+ * stay valid until the dataset has been packed, i.e. until the first request
+ * on it completes) and returns its id.  gbmi_server_submit queues the
+ * all-pairs problem of dataset a (b = -1) or the cross problem between a and
+ * b (same m) and returns a ticket.  gbmi_server_wait blocks until the ticket
+ * is done (or timeout_ms, 0 = forever), then gives the device pointer of the
+ * FP32 result (n_a x n_a or n_a x n_b, valid until gbmi_server_release) and
+ * the latency from submit to completion in ms.  gbmi_server_stats fills
+ * stats[0..7] = completed requests, p50 ms, p99 ms, mean ms, max ms, pairs
+ * per second over the server's busy span, batches launched, mean requests
+ * per batch.  The server reads X on its own streams: its contents must be
+ * complete on the device when the dataset is added.  Memory is returned by
+ * gbmi_server_release (outputs) and gbmi_server_remove_dataset (datasets,
+ * once no queued or running request reads them); a request that does not fit
+ * waits in the queue until enough is returned.  Limits: m <= 2^24 per
+ * dataset; a request whose memory could not fit even an empty arena fails
+ * with GBMI_ERR_OOM at submit.  gbmi_server_destroy lets the running batches
+ * finish, fails the queued requests, and frees the arena (result pointers
+ * become invalid). */
+typedef struct gbmi_server gbmi_server;
+
+gbmi_status gbmi_server_create(int64_t budget_bytes, int max_batch, gbmi_server** srv);
+gbmi_status gbmi_server_add_dataset(gbmi_server* srv, const uint8_t* X, int64_t m, int64_t n,
+                                    int64_t* id);
+gbmi_status gbmi_server_remove_dataset(gbmi_server* srv, int64_t id);
+gbmi_status gbmi_server_submit(gbmi_server* srv, int64_t a, int64_t b, int64_t* ticket);
+gbmi_status gbmi_server_wait(gbmi_server* srv, int64_t ticket, int64_t timeout_ms,
+                             const float** out, double* latency_ms);
+gbmi_status gbmi_server_release(gbmi_server* srv, int64_t ticket);
+gbmi_status gbmi_server_stats(gbmi_server* srv, double* stats);
+gbmi_status gbmi_server_destroy(gbmi_server* srv);
+
 /* Tile-width table of the autotuner (no counterpart in the paper).  The
  * tensor-core Gram works on tiles of 128 x tile_n variable pairs; narrow tiles
  * waste less padding on small n, wide tiles stream fewer operand bytes per

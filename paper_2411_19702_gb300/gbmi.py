@@ -83,6 +83,14 @@ def load(path: str | None = None):
             "gbmi_batch_set_io": [vp, vp, i32],
             "gbmi_batch_destroy": [vp],
             "gbmi_mi_batch": [vp, i32],
+            "gbmi_server_create": [i64, i32, vp],
+            "gbmi_server_add_dataset": [vp, vp, i64, i64, vp],
+            "gbmi_server_remove_dataset": [vp, i64],
+            "gbmi_server_submit": [vp, i64, i64, vp],
+            "gbmi_server_wait": [vp, i64, i64, vp, vp],
+            "gbmi_server_release": [vp, i64],
+            "gbmi_server_stats": [vp, vp],
+            "gbmi_server_destroy": [vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -432,3 +440,96 @@ def profile(enable: bool | None = None, reset: bool = False) -> dict:
         out[lib.gbmi_profile_name(k).decode()] = {"ms": float(lib.gbmi_profile_ms(k)),
                                                   "launches": int(lib.gbmi_profile_launches(k))}
     return out
+
+
+class _DeviceView:
+    """A device buffer the server owns, exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4",
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+class Server:
+    """Request loop with continuous batching over resident datasets.
+
+    ``add_dataset(X)`` registers a device uint8 0/1 matrix (kept referenced
+    until ``remove_dataset``); ``submit(a)`` / ``submit(a, b)`` queue the
+    all-pairs or cross MI problem and return a ticket; ``wait(ticket)``
+    returns ``(mi, latency_ms)`` where ``mi`` is a zero-copy float32 view of
+    the server's output buffer, valid until ``release(ticket)``.
+    """
+
+    def __init__(self, budget_bytes: int, max_batch: int = 64, device=None):
+        import torch
+        self._dev = torch.device("cuda", torch.cuda.current_device() if device is None
+                                 else torch.device(device).index or 0)
+        self._srv = ctypes.c_void_p()
+        self._data: dict[int, object] = {}
+        self._shape: dict[int, tuple] = {}
+        self._tshape: dict[int, tuple] = {}
+        with torch.cuda.device(self._dev):
+            _check(load().gbmi_server_create(int(budget_bytes), int(max_batch),
+                                             ctypes.byref(self._srv)))
+
+    def add_dataset(self, X) -> int:
+        import torch
+        X = _prep(X)
+        if X.device != self._dev:
+            raise ValueError(f"X is on {X.device}, the server on {self._dev}")
+        torch.cuda.current_stream(X.device).synchronize()
+        i = ctypes.c_int64()
+        _check(load().gbmi_server_add_dataset(self._srv, X.data_ptr(), X.shape[0], X.shape[1],
+                                              ctypes.byref(i)))
+        self._data[i.value] = X
+        self._shape[i.value] = tuple(X.shape)
+        return i.value
+
+    def remove_dataset(self, ds: int):
+        _check(load().gbmi_server_remove_dataset(self._srv, int(ds)))
+        self._data.pop(ds, None)
+
+    def submit(self, a: int, b: int | None = None) -> int:
+        t = ctypes.c_int64()
+        _check(load().gbmi_server_submit(self._srv, int(a), -1 if b is None else int(b),
+                                         ctypes.byref(t)))
+        na = self._shape[a][1]
+        self._tshape[t.value] = (na, na if b is None else self._shape[b][1])
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 0):
+        import torch
+        p, lat = ctypes.c_void_p(), ctypes.c_double()
+        _check(load().gbmi_server_wait(self._srv, int(ticket), int(timeout_ms), ctypes.byref(p),
+                                       ctypes.byref(lat)))
+        view = torch.as_tensor(_DeviceView(p.value, self._tshape[ticket]), device=self._dev)
+        return view, lat.value
+
+    def release(self, ticket: int):
+        _check(load().gbmi_server_release(self._srv, int(ticket)))
+        self._tshape.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = (ctypes.c_double * 8)()
+        _check(load().gbmi_server_stats(self._srv, st))
+        keys = ("completed", "p50_ms", "p99_ms", "mean_ms", "max_ms", "pairs_per_s", "batches",
+                "requests_per_batch")
+        return dict(zip(keys, list(st)))
+
+    def close(self):
+        if self._srv:
+            _check(load().gbmi_server_destroy(self._srv))
+            self._srv = ctypes.c_void_p()
+            self._data.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

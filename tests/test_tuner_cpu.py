@@ -67,3 +67,20 @@ def test_batch_argument_errors_need_no_gpu():
     jobs[0] = gbmi._Job(16, 0, (1 << 24) + 1, 4, 0, 32)   # m beyond the fused limit
     assert lib.gbmi_batch_create(jobs, 1, ctypes.byref(plan)) == gbmi.ERR_ARG
     assert b"2^24" in lib.gbmi_last_error_string()
+
+
+def test_server_argument_errors_need_no_gpu():
+    lib = gbmi.load()
+    srv = ctypes.c_void_p()
+    assert lib.gbmi_server_create(1024, 4, ctypes.byref(srv)) == gbmi.ERR_ARG   # budget < 1 MiB
+    assert not srv.value
+    assert lib.gbmi_server_create(1 << 30, 0, ctypes.byref(srv)) == gbmi.ERR_ARG
+    assert b"max_batch" in lib.gbmi_last_error_string()
+    i = ctypes.c_int64()
+    assert lib.gbmi_server_add_dataset(None, 16, 10, 4, ctypes.byref(i)) == gbmi.ERR_ARG
+    assert lib.gbmi_server_submit(None, 0, -1, ctypes.byref(i)) == gbmi.ERR_ARG
+    assert lib.gbmi_server_wait(None, 0, 0, None, None) == gbmi.ERR_ARG
+    assert lib.gbmi_server_release(None, 0) == gbmi.ERR_ARG
+    assert lib.gbmi_server_remove_dataset(None, 0) == gbmi.ERR_ARG
+    assert lib.gbmi_server_stats(None, None) == gbmi.ERR_ARG
+    assert lib.gbmi_server_destroy(None) == gbmi.OK
