@@ -56,6 +56,26 @@ def _env_int(name, default):
         return default
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """Maximum of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of weakly scaled replicas: all ranks' units / slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s replica: every rank solves its own independent problem."""
+    return base + rank
+
+
 def _workload(m, n):
     return {"workload": f"paper-scale all-pairs MI, m={m} samples x n={n} variables, "
                         "p_j~Beta(0.5,5), 1% planted noisy copies",
@@ -473,14 +493,11 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def reduce_max(x):
+        return max_over_ranks(x, dist, dev)
 
-    X, info = simdata.make(m, n, simdata.PAPER.seed + rank, "beta", 0.01, 0.05, device=str(dev))
+    X, info = simdata.make(m, n, replica_seed(simdata.PAPER.seed, rank), "beta", 0.01, 0.05,
+                           device=str(dev))
     out = torch.empty((n, n), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -542,7 +559,7 @@ def run_ours(args):
                   "ok": err <= 1e-6}
 
     fused = timed("fused", args.steps, args.warmup, sample_clocks=True, profile=False)
-    fused_ms = max_over_ranks(fused["ms"])
+    fused_ms = reduce_max(fused["ms"])
     # the same loop again with the event profiler on: per-kernel device times
     prof = timed("fused", max(3, min(args.steps, 20)), 1, profile=True)["profile"]
     plain = timed("plain", max(3, min(args.steps, 20)), 2, profile=True)
@@ -581,8 +598,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             gbmi.mi_all_pairs_host(Xh, outh)
-        dt = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
-        e2e = {"value": world * pairs / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+        dt = reduce_max((time.perf_counter() - t0) / e2e_steps)
+        e2e = {"value": whole_job_rate(pairs, world, dt), "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int(m) * n, "d2h_bytes_per_step": int(n) * n * 4}
 
     # FP64 oracle on the host cores, bounded sample (rank 0, N=1 only)
@@ -601,9 +618,9 @@ def run_ours(args):
     if not args.skip_serve and rank == 0:
         serving = measure_serving(dev, seconds=args.serve_seconds)
 
-    value = world * pairs / (fused_ms * 1e-3)
-    plain_ms = max_over_ranks(plain["ms"])
-    popc_ms = max_over_ranks(popc["ms"])
+    value = whole_job_rate(pairs, world, fused_ms * 1e-3)
+    plain_ms = reduce_max(plain["ms"])
+    popc_ms = reduce_max(popc["ms"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": fused_ms,
@@ -613,14 +630,14 @@ def run_ours(args):
         "config": dict(_workload(m, n), path="fused",
                        arithmetic="FP8 E4M3 0/1 operands, FP32 tensor-core accumulation "
                                   "(exact counts), FP32 epilogue, FP64 combine below 1e-4"),
-        "plain": {"value": world * pairs / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+        "plain": {"value": whole_job_rate(pairs, world, plain_ms * 1e-3), "ms_per_step": plain_ms,
                   "path": "tcgen05 Gram -> int32 N11 in HBM -> elementwise MI kernel",
                   "kernels": {k: v["ms"] / max(v["launches"], 1)
                               for k, v in (plain["profile"] or {}).items()}},
         "fixup_toggled": {"fp64_combine": bool(1 - fix_default),
-                          "value": world * pairs / (max_over_ranks(alt["ms"]) * 1e-3),
-                          "ms_per_step": max_over_ranks(alt["ms"])},
-        "popcount": {"value": world * pairs / (popc_ms * 1e-3), "ms_per_step": popc_ms},
+                          "value": whole_job_rate(pairs, world, reduce_max(alt["ms"]) * 1e-3),
+                          "ms_per_step": reduce_max(alt["ms"])},
+        "popcount": {"value": whole_job_rate(pairs, world, popc_ms * 1e-3), "ms_per_step": popc_ms},
         "fused_over_plain": plain_ms / fused_ms,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
