@@ -84,6 +84,33 @@ def _workload(m, n):
             "parallelism": "replicas (one independent problem per GPU)"}
 
 
+POPC_PER_CLK_PER_SM = 16   # 32-bit population counts per clock per SM (integer pipe)
+
+
+def _fp8_gemm_tflops(dev, size=8192, reps=10):
+    """cuBLASLt FP8 E4M3 GEMM rate (torch._scaled_mm, best of `reps`): context only."""
+    import torch
+    try:
+        a = torch.randn(size, size, device=dev).to(torch.float8_e4m3fn)
+        b = torch.randn(size, size, device=dev).to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        f = lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        for _ in range(3):
+            f()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        return 2.0 * size ** 3 / (best * 1e-3) / 1e12
+    except Exception:
+        return None
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -316,6 +343,47 @@ def measure_batch(dev, reps=3, k=512, seed=4):
     plan.close()
     gbmi.tuner_clear()
     del Xs, outs, sep_out
+    torch.cuda.empty_cache()
+    return res
+
+
+# --------------------------------------------------------------- out-of-core output
+def measure_out_of_core(dev, m=100_000, n=50_000, reps=2, seed=6):
+    """All-pairs MI of n = 50,000 variables in row panels into page-locked host memory
+    (10 GB of output), against the in-core fused call on the same input."""
+    import torch
+
+    from paper_2411_19702_gb300 import gbmi
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    X = _beta_matrix(m, n, g, rng, dev)
+    pairs = n * (n - 1) // 2
+    host = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+    gbmi.mi_all_pairs_to_host(X, out=host)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        gbmi.mi_all_pairs_to_host(X, out=host)
+    ooc_s = (time.perf_counter() - t0) / reps
+    dev_out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    gbmi.mi_all_pairs(X, out=dev_out, path="fused")
+    gbmi.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        gbmi.mi_all_pairs(X, out=dev_out, path="fused")
+    e1.record()
+    torch.cuda.synchronize(dev)
+    in_s = e0.elapsed_time(e1) / reps * 1e-3
+    rows = torch.arange(0, n, 997, device=dev)
+    same = bool(torch.equal(host[rows.cpu()], dev_out[rows].cpu()))
+    res = {"m": m, "n": n, "output_bytes": n * n * 4, "host_memory": "page-locked",
+           "to_host_s": ooc_s, "to_host_pairs_per_s": pairs / ooc_s,
+           "d2h_gbs": n * n * 4 / ooc_s / 1e9,
+           "in_core_device_s": in_s, "in_core_pairs_per_s": pairs / in_s,
+           "to_host_over_in_core": ooc_s / in_s,
+           "rows_checked_bit_identical": same}
+    del X, dev_out, host
     torch.cuda.empty_cache()
     return res
 
@@ -581,6 +649,13 @@ def run_ours(args):
     achieved = flops / (gram_ms * 1e-3) / 1e12
     peak = 2.0 * peaks["bf16_tflops"]           # FP8 = 2 x measured BF16 (nominal ratio)
     traffic, tsrc = _profiled_traffic()
+    cublas_fp8 = _fp8_gemm_tflops(dev)
+    # popcount path: ALU-bound on the population-count rate, one POPC per 32-bit word pair
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = (fused["clocks"] or {}).get("sm_mhz") or peaks["sm_max_mhz"]
+    words = (m + 31) // 32
+    popc_rate = pairs * words / (popc["ms"] * 1e-3)
+    popc_peak = sm_count * POPC_PER_CLK_PER_SM * clk_mhz * 1e6
     step_total = sum(v["ms"] for v in prof.values())
     kernels = {k: {"ms_per_launch": v["ms"] / max(v["launches"], 1),
                    "launches": v["launches"],
@@ -614,6 +689,9 @@ def run_ours(args):
     batch = None
     if not args.skip_batch:
         batch = measure_batch(dev)
+    out_of_core = None
+    if not args.skip_ooc and rank == 0:
+        out_of_core = measure_out_of_core(dev)
     serving = None
     if not args.skip_serve and rank == 0:
         serving = measure_serving(dev, seconds=args.serve_seconds)
@@ -637,13 +715,21 @@ def run_ours(args):
         "fixup_toggled": {"fp64_combine": bool(1 - fix_default),
                           "value": whole_job_rate(pairs, world, reduce_max(alt["ms"]) * 1e-3),
                           "ms_per_step": reduce_max(alt["ms"])},
-        "popcount": {"value": whole_job_rate(pairs, world, popc_ms * 1e-3), "ms_per_step": popc_ms},
+        "popcount": {"value": whole_job_rate(pairs, world, popc_ms * 1e-3), "ms_per_step": popc_ms,
+                     "roofline": {"bound": "alu", "achieved": popc_rate / 1e12,
+                                  "peak": popc_peak / 1e12, "unit": "Tpopc/s",
+                                  "frac": popc_rate / popc_peak,
+                                  "peak_source": f"{sm_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk "
+                                                 f"x {clk_mhz:.0f} MHz (median SM clock)",
+                                  "words_per_pair": words}},
         "fused_over_plain": plain_ms / fused_ms,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "gram_tc_fused_mi",
                      "peak_source": f"{peaks['source']} bf16 burst x 2 (FP8/BF16 nominal ratio)",
                      "flops_per_launch": flops, "ms_per_launch": gram_ms,
+                     "context_cublas_fp8_tflops": cublas_fp8,
+                     "frac_of_cublas_fp8": achieved / cublas_fp8 if cublas_fp8 else None,
                      "traffic_source": tsrc},
         "kernels": kernels,
         "clocks": fused["clocks"],
@@ -651,6 +737,7 @@ def run_ours(args):
         "parity": parity,
         "batch": batch,
         "serving": serving,
+        "out_of_core": out_of_core,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
@@ -674,6 +761,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-ooc", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -125,6 +125,29 @@ gbmi_status mi_cross_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t
  * host threads or streams) race and must not be issued. */
 gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t n, float* out);
 
+/* ------------------------------------------------------ out-of-core output */
+
+/* Out-of-core output (the blockwise computation the paper names as future
+ * work, Sec. 5): for n where the n x n FP32 matrix does not fit in device
+ * memory (n^2 * 4 bytes; n ~ 260,000 fills a GB300), or a cross problem with
+ * a very large n2.  X (and Y) are device pointers as for mi_all_pairs /
+ * mi_cross and must fit on the device together with their packed copy; the
+ * result goes to host_out, HOST memory, row-major n x n (or n1 x n2), which
+ * should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to
+ * overlap the computation.  The matrix is computed in row panels of
+ * panel_rows variables (0: automatic, within 4 GiB of device staging and at
+ * least about eight panels) by the fused tensor-core path into two device
+ * staging slots; each panel is copied to the host on a second stream while
+ * the next one computes.  For all pairs, panel [i0, i1) computes rows
+ * [i0, i1) x columns [i0, n) and writes the mirror of that block as well, so
+ * every off-diagonal pair is evaluated once.  Values are bit-identical to
+ * mi_all_pairs / mi_cross.  Synchronous: returns when host_out is complete.
+ * Needs m <= 2^24 (the fused path's exact FP32 range). */
+gbmi_status gbmi_mi_all_pairs_to_host(const uint8_t* X, int64_t m, int64_t n, float* host_out,
+                                      int64_t panel_rows);
+gbmi_status gbmi_mi_cross_to_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
+                                  int64_t n2, float* host_out, int64_t panel_rows);
+
 /* ------------------------------------------------------ counts and pieces */
 
 /* Co-occurrence counts N11 = X^T X (G11 of Sec. 2 step 2) as int32, n x n,

@@ -346,6 +346,171 @@ gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
     return GBMI_OK;
 }
 
+// Device staging of the out-of-core path (both slots, panel and mirror).
+constexpr int64_t kStagingBytes = int64_t{4} << 30;
+
+// Out-of-core output: the MI matrix in row panels, each computed into one of
+// two device staging slots by the fused Gram and copied to host memory on a
+// second stream while the next panel computes.  All pairs: panel [i0, i1)
+// computes the block rows [i0, i1) x columns [i0, n) once and also writes its
+// mirror (columns [i0, i1) of rows [i1, n)), so the host receives the full
+// symmetric matrix with no pair computed twice off the diagonal blocks.
+gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
+                         float* host_out, int64_t panel, bool sym) {
+    if (X == nullptr || host_out == nullptr || (!sym && Y == nullptr))
+        return fail(GBMI_ERR_ARG, "null pointer");
+    GBMI_TRY(check_sizes(m, n1, n2));
+    if (m > kExactChunk) return fail(GBMI_ERR_ARG, "the out-of-core path needs m <= 2^24");
+    if (panel < 0) return fail(GBMI_ERR_ARG, "panel_rows must be >= 0");
+    DeviceCtx* cp = nullptr;
+    GBMI_TRY(rt::get_ctx(&cp));
+    DeviceCtx& c = *cp;
+    if (panel == 0) {
+        const int64_t per_row = (sym ? 2 : 1) * n2 * 4;          // staging bytes per panel row
+        panel = std::max<int64_t>(1, kStagingBytes / 2 / per_row);
+        if (panel >= kTcBM) panel = panel / kTcBM * kTcBM;
+        // at least about eight panels, so that copies overlap the computation
+        const int64_t eighth = (n1 + 8 * kTcBM - 1) / (8 * kTcBM) * kTcBM;
+        panel = std::min(panel, std::max<int64_t>(kTcBM, eighth));
+    }
+    panel = std::min(panel, n1);
+    const int64_t panels = (n1 + panel - 1) / panel;
+
+    TcLayout L;
+    GBMI_TRY(tc_prepare(c, X, Y, m, n1, n2, sym, &L));
+    MiParams mp;
+    GBMI_TRY(rt::mi_params(c, m, &mp));
+    const MiVar *va = nullptr, *vb = nullptr;
+    GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.va.p), n1, mp, c.ha, &va));
+    if (sym)
+        vb = va;
+    else
+        GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.vb.p), n2, mp, c.hb, &vb));
+
+    // every panel's job and tile list, uploaded once
+    const int group = std::max(1, g_opt.group_cols);
+    std::vector<GramJob> jobs(static_cast<size_t>(panels));
+    std::vector<int64_t> first(static_cast<size_t>(panels) + 1, 0);
+    for (int64_t p = 0; p < panels; ++p) {
+        const int64_t i0 = p * panel, rows = std::min(panel, n1 - i0);
+        const int64_t j0 = sym ? i0 : 0, w = n2 - j0;
+        GramJob& g = jobs[static_cast<size_t>(p)];
+        std::memset(&g, 0, sizeof(g));
+        g.rowA = i0;
+        g.strideA = L.rows_a;
+        g.rowB = sym ? i0 : L.kb * L.rows_a;
+        g.strideB = sym ? L.rows_a : L.rows_b;
+        g.k_begin = 0;
+        g.k_blocks = static_cast<int32_t>(L.kb);
+        g.n_a = static_cast<int32_t>(rows);
+        g.n_b = static_cast<int32_t>(w);
+        g.symmetric = 0;
+        g.bn = rt::choose_bn(m, rows, w, false);
+        g.vec_store = (w % 4 == 0) ? 1 : 0;
+        g.va = va + i0;
+        g.vb = vb + j0;
+        g.ld_out = w;
+        g.ld_t = rows;
+        g.mp = mp;
+        first[static_cast<size_t>(p) + 1] = first[static_cast<size_t>(p)] +
+                                            gram_tile_count(rows, w, g.bn, false);
+    }
+    const int64_t total_tiles = first.back();
+    std::vector<GramTile> tiles(static_cast<size_t>(total_tiles));
+    for (int64_t p = 0; p < panels; ++p) {
+        const GramJob& g = jobs[static_cast<size_t>(p)];
+        if (first[p + 1] - first[p] > 0x7FFFFFFF) return fail(GBMI_ERR_ARG, "too many tiles");
+        gram_tiles(0, g.n_a, g.n_b, g.bn, false, group, tiles.data() + first[p]);
+    }
+
+    const size_t up_bytes = static_cast<size_t>(panel) * n2 * 4;
+    const size_t lo_bytes = sym ? static_cast<size_t>(n2) * panel * 4 : 0;
+    DevBuf up[2], lo[2], tl;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        if (cs) cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(g_stream);
+        for (int s = 0; s < 2; ++s) {
+            if (computed[s]) cudaEventDestroy(computed[s]);
+            if (copied[s]) cudaEventDestroy(copied[s]);
+            rt::release(up[s]);
+            rt::release(lo[s]);
+        }
+        rt::release(tl);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    gbmi_status st = [&]() -> gbmi_status {
+        for (int s = 0; s < 2 && s < panels; ++s) {
+            GBMI_TRY(ensure(up[s], up_bytes, "panel staging"));
+            if (sym) GBMI_TRY(ensure(lo[s], lo_bytes, "mirror staging"));
+            GBMI_CUDA(cudaEventCreateWithFlags(&computed[s], cudaEventDisableTiming), "event");
+            GBMI_CUDA(cudaEventCreateWithFlags(&copied[s], cudaEventDisableTiming), "event");
+        }
+        GBMI_TRY(ensure(tl, tiles.size() * sizeof(GramTile), "tile list"));
+        GBMI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "copy stream");
+        GBMI_CUDA(cudaMemcpyAsync(tl.p, tiles.data(), tiles.size() * sizeof(GramTile),
+                                  cudaMemcpyHostToDevice, g_stream),
+                  "tile list upload");
+        OperandMaps maps;
+        if (!make_operand_maps(&maps, static_cast<const uint8_t*>(c.P.p), L.total_rows))
+            return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        GBMI_TRY(ensure(c.sched, 256, "tile counter"));
+        for (int64_t p = 0; p < panels; ++p) {
+            const int s = static_cast<int>(p & 1);
+            const int64_t i0 = p * panel, rows = std::min(panel, n1 - i0);
+            const int64_t j0 = sym ? i0 : 0, w = n2 - j0;
+            if (p >= 2) GBMI_CUDA(cudaStreamWaitEvent(g_stream, copied[s], 0), "wait copy");
+            GramLaunch G;
+            std::memset(&G, 0, sizeof(G));
+            G.job0 = jobs[static_cast<size_t>(p)];
+            G.job0.out_f = static_cast<float*>(up[s].p);
+            G.job0.out_t = sym ? static_cast<float*>(lo[s].p) : nullptr;
+            G.tiles = static_cast<const GramTile*>(tl.p) + first[p];
+            G.num_tiles = static_cast<int>(first[p + 1] - first[p]);
+            G.mode = kTcModeMI;
+            G.err = static_cast<unsigned int*>(c.err.p);
+            G.timeout_ns = g_opt.timeout_ns;
+            G.debug_flags = g_opt.debug_flags;
+            G.counter = static_cast<unsigned int*>(c.sched.p);
+            GBMI_CUDA(cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
+            GBMI_LAUNCH(launch_gram_tc(maps, G, rt::grid_for(c, G.num_tiles), g_stream),
+                        "gram_tc_fused_mi");
+            GBMI_CUDA(cudaEventRecord(computed[s], g_stream), "event");
+            GBMI_CUDA(cudaStreamWaitEvent(cs, computed[s], 0), "wait panel");
+            if (sym) {
+                GBMI_CUDA(cudaMemcpy2DAsync(host_out + i0 * n2 + i0, n2 * 4, up[s].p, w * 4, w * 4,
+                                            rows, cudaMemcpyDeviceToHost, cs),
+                          "panel copy");
+                if (w > rows)
+                    GBMI_CUDA(cudaMemcpy2DAsync(host_out + (i0 + rows) * n2 + i0, n2 * 4,
+                                                static_cast<float*>(lo[s].p) + rows * rows,
+                                                rows * 4, rows * 4, w - rows,
+                                                cudaMemcpyDeviceToHost, cs),
+                              "mirror copy");
+            } else {
+                GBMI_CUDA(cudaMemcpyAsync(host_out + i0 * n2, up[s].p,
+                                          static_cast<size_t>(rows) * n2 * 4,
+                                          cudaMemcpyDeviceToHost, cs),
+                          "panel copy");
+            }
+            GBMI_CUDA(cudaEventRecord(copied[s], cs), "event");
+        }
+        GBMI_CUDA(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
+        GBMI_CUDA(cudaStreamSynchronize(g_stream), "cudaStreamSynchronize");
+        unsigned int err = 0;
+        GBMI_CUDA(cudaMemcpy(&err, c.err.p, sizeof(err), cudaMemcpyDeviceToHost),
+                  "read error word");
+        if (err != 0) {
+            cudaMemset(c.err.p, 0, sizeof(err));
+            return fail(GBMI_ERR_TIMEOUT, "a bounded device-side wait timed out");
+        }
+        return GBMI_OK;
+    }();
+    cleanup();
+    return st;
+}
+
 }  // namespace
 }  // namespace gbmi
 
@@ -386,6 +551,18 @@ gbmi_status mi_cross_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t
                           float* out) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     return host_impl(X, Y, m, n1, n2, out, false);
+}
+
+gbmi_status gbmi_mi_all_pairs_to_host(const uint8_t* X, int64_t m, int64_t n, float* host_out,
+                                      int64_t panel_rows) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    return blocked_impl(X, nullptr, m, n, n, host_out, panel_rows, true);
+}
+
+gbmi_status gbmi_mi_cross_to_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
+                                  int64_t n2, float* host_out, int64_t panel_rows) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    return blocked_impl(X, Y, m, n1, n2, host_out, panel_rows, false);
 }
 
 gbmi_status gbmi_counts_all_pairs(const uint8_t* X, int64_t m, int64_t n, int32_t* n11,

@@ -26,8 +26,9 @@
 //               load 16 accumulator columns at a time (one TMEM lane = one
 //               variable i per thread), derive n10, n01, n00, evaluate MI and
 //               store (i, j) as 16-byte vectors and, for a symmetric problem,
-//               (j, i) as coalesced rows.  The second accumulator lets tile
-//               t+1's MMAs run meanwhile.
+//               (j, i) as coalesced rows (or, for a panel of an out-of-core
+//               run, (j, i) into a separate mirror buffer).  The second
+//               accumulator lets tile t+1's MMAs run meanwhile.
 // Tiles come from a host-built list: for all-pairs only blocks that touch
 // the upper triangle (j >= i), in groups of column blocks, jobs one after
 // another, so that CTAs running at the same time share operand panels in L2.
@@ -420,6 +421,14 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
                 for (int q = 0; q < kGroup; ++q) {
                     const int64_t j = j0 + q;
                     if (j < n_b && j > i) store_one<kMode>(job, j, i, r[q]);
+                }
+            }
+            // mirror into a separate buffer (panels of an out-of-core run)
+            if (kMode == kTcModeMI && job.out_t != nullptr && row_ok) {
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) {
+                    const int64_t j = j0 + q;
+                    if (j < n_b) job.out_t[j * job.ld_t + i] = __uint_as_float(r[q]);
                 }
             }
             // (i, j): 16 consecutive columns of this thread's row

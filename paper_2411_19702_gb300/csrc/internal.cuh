@@ -114,6 +114,8 @@ struct GramJob {
     float* out_f;
     int32_t* out_c;
     int64_t ld_out;
+    float* out_t;              // MI mode, or null: also write (j, i) to out_t[j * ld_t + i]
+    int64_t ld_t;
     MiParams mp;
 };
 

@@ -83,6 +83,8 @@ def load(path: str | None = None):
             "gbmi_batch_set_io": [vp, vp, i32],
             "gbmi_batch_destroy": [vp],
             "gbmi_mi_batch": [vp, i32],
+            "gbmi_mi_all_pairs_to_host": [vp, i64, i64, vp, i64],
+            "gbmi_mi_cross_to_host": [vp, vp, i64, i64, i64, vp, i64],
             "gbmi_server_create": [i64, i32, vp],
             "gbmi_server_add_dataset": [vp, vp, i64, i64, vp],
             "gbmi_server_remove_dataset": [vp, i64],
@@ -289,6 +291,48 @@ def mi_cross_host(X, Y, out=None):
     if out is None:
         out = np.empty((n1, n2), dtype=np.float32)
     _check(load().mi_cross_host(Xn.ctypes.data, Yn.ctypes.data, m, n1, n2, out.ctypes.data))
+    return out
+
+
+def _host_out(shape, out):
+    import torch
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    if (out.is_cuda or tuple(out.shape) != tuple(shape) or out.dtype != torch.float32
+            or not out.is_contiguous()):
+        raise ValueError(f"out must be a contiguous float32 host tensor of shape {shape}")
+    return out
+
+
+def mi_all_pairs_to_host(X, out=None, panel_rows=0):
+    """n x n MI matrix of X (device) computed in row panels straight into host memory.
+
+    ``out`` defaults to a page-locked host tensor; panel_rows = 0 picks the
+    panel height automatically.  Returns ``out`` when complete.
+    """
+    import torch
+    X = _prep(X)
+    m, n = X.shape
+    out = _host_out((n, n), out)
+    with torch.cuda.device(X.device):
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_mi_all_pairs_to_host(X.data_ptr(), m, n, out.data_ptr(), int(panel_rows)))
+    return out
+
+
+def mi_cross_to_host(X, Y, out=None, panel_rows=0):
+    """n1 x n2 MI matrix between the columns of X and Y, in row panels into host memory."""
+    import torch
+    X, Y = _prep(X), _prep(Y, "Y")
+    m, n1 = X.shape
+    if Y.shape[0] != m:
+        raise ValueError("X and Y must have the same number of samples")
+    n2 = Y.shape[1]
+    out = _host_out((n1, n2), out)
+    with torch.cuda.device(X.device):
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_mi_cross_to_host(X.data_ptr(), Y.data_ptr(), m, n1, n2, out.data_ptr(),
+                                         int(panel_rows)))
     return out
 
 

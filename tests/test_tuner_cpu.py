@@ -84,3 +84,13 @@ def test_server_argument_errors_need_no_gpu():
     assert lib.gbmi_server_remove_dataset(None, 0) == gbmi.ERR_ARG
     assert lib.gbmi_server_stats(None, None) == gbmi.ERR_ARG
     assert lib.gbmi_server_destroy(None) == gbmi.OK
+
+
+def test_out_of_core_argument_errors_need_no_gpu():
+    lib = gbmi.load()
+    assert lib.gbmi_mi_all_pairs_to_host(None, 10, 4, 16, 0) == gbmi.ERR_ARG
+    assert lib.gbmi_mi_all_pairs_to_host(16, 10, 4, None, 0) == gbmi.ERR_ARG
+    assert lib.gbmi_mi_all_pairs_to_host(16, 10, 4, 16, -1) == gbmi.ERR_ARG
+    assert b"panel_rows" in lib.gbmi_last_error_string()
+    assert lib.gbmi_mi_all_pairs_to_host(16, (1 << 24) + 1, 4, 16, 0) == gbmi.ERR_ARG
+    assert lib.gbmi_mi_cross_to_host(16, None, 10, 4, 4, 16, 0) == gbmi.ERR_ARG
