@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 
 #include "runtime.h"
 
@@ -23,6 +24,17 @@ using rt::g_stream;
 constexpr int64_t kExactChunk = int64_t{1} << 24;
 // AUTO uses the popcount path when the Gram work is this small (m * n * n).
 constexpr double kTinyWork = 6.0e7;
+
+// Status for a non-zero device error word.
+gbmi_status error_word_status(unsigned int err) {
+    if (err & kErrBadOperand)
+        return fail(GBMI_ERR_ARG, "a direct operand copy was not 16-byte aligned (skipped)");
+    if ((err & ~static_cast<unsigned int>(kErrNotBinary)) != 0)
+        return fail(GBMI_ERR_TIMEOUT, "a bounded device-side wait timed out (code " +
+                                          std::to_string(err) + ")");
+    return fail(GBMI_ERR_NOT_BINARY,
+                "the direct operand path met a byte other than 0 / 1 (the result is unspecified)");
+}
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
     const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -91,10 +103,13 @@ gbmi_status tile_list(DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn, 
 
 // Run the tensor-core Gram of one job over [0, m) in exact chunks.  mode MI
 // needs one chunk (m <= 2^24); the counts modes add chunk results into out_c.
+// direct: the operands are the caller's matrices through *dmaps (no pack).
 gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int64_t m,
-                     int mode) {
+                     int mode, const OperandMaps* dmaps = nullptr) {
     OperandMaps maps;
-    if (!make_operand_maps(&maps, static_cast<const uint8_t*>(c.P.p), total_rows))
+    if (dmaps != nullptr)
+        maps = *dmaps;
+    else if (!make_operand_maps(&maps, static_cast<const uint8_t*>(c.P.p), total_rows))
         return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     int tiles = 0;
     GBMI_TRY(tile_list(c, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn, &tiles));
@@ -107,6 +122,7 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     L.err = static_cast<unsigned int*>(c.err.p);
     L.timeout_ns = g_opt.timeout_ns;
     L.debug_flags = g_opt.debug_flags;
+    L.direct = dmaps != nullptr ? 1 : 0;
     GBMI_TRY(ensure(c.sched, 256, "tile counter"));
     L.counter = static_cast<unsigned int*>(c.sched.p);
     const int64_t kb_total = pack_ld(m) / kTcBK;
@@ -132,13 +148,46 @@ int choose_path(int path, int64_t m, int64_t n1, int64_t n2) {
     return GBMI_PATH_FUSED;
 }
 
-// Workspace layout of the tensor-core path: X's operand rows, then Y's.
+// Workspace layout of the tensor-core path: X's operand rows, then Y's; or,
+// for the direct path, the tensor maps over X and Y themselves.
 struct TcLayout {
     int64_t kb, rows_a, rows_b, total_rows;
+    bool direct;
+    OperandMaps maps;
 };
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// The direct path (no pack: the tensor cores read X and Y as MN-major E4M3)
+// applies when it is enabled and the rows of X and Y are 16-byte multiples.
+bool direct_ok(const uint8_t* X, const uint8_t* Y, int64_t n1, int64_t n2, bool sym) {
+    return g_opt.direct != 0 && n1 % 16 == 0 && aligned16(X) &&
+           (sym || (n2 % 16 == 0 && aligned16(Y)));
+}
 
 gbmi_status tc_prepare(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
                        int64_t n2, bool sym, TcLayout* L) {
+    L->direct = direct_ok(X, Y, n1, n2, sym);
+    if (L->direct) {
+        L->kb = pack_ld(m) / kTcBK;
+        L->rows_a = L->rows_b = L->total_rows = 0;
+        if (!make_direct_maps(&L->maps, X, m, n1, sym ? X : Y, sym ? n1 : n2))
+            return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        unsigned int* err = static_cast<unsigned int*>(c.err.p);
+        GBMI_TRY(ensure(c.va, static_cast<size_t>(n1) * 4, "column counts"));
+        GBMI_LAUNCH(launch_zero_u32(c.va.p, n1, g_stream), "zero");
+        GBMI_LAUNCH(launch_colsum_direct(X, m, n1, static_cast<int32_t*>(c.va.p), err,
+                                         c.sm_count, g_stream),
+                    "colsum_direct");
+        if (!sym) {
+            GBMI_TRY(ensure(c.vb, static_cast<size_t>(n2) * 4, "column counts"));
+            GBMI_LAUNCH(launch_zero_u32(c.vb.p, n2, g_stream), "zero");
+            GBMI_LAUNCH(launch_colsum_direct(Y, m, n2, static_cast<int32_t*>(c.vb.p), err,
+                                             c.sm_count, g_stream),
+                        "colsum_direct");
+        }
+        return GBMI_OK;
+    }
     L->kb = pack_ld(m) / kTcBK;
     L->rows_a = pack_rows(n1);
     L->rows_b = sym ? 0 : pack_rows(n2);
@@ -166,6 +215,11 @@ GramJob tc_job(const TcLayout& L, int64_t m, int64_t n1, int64_t n2, bool sym, i
     g.strideA = L.rows_a;
     g.rowB = sym ? 0 : L.kb * L.rows_a;
     g.strideB = sym ? L.rows_a : L.rows_b;
+    if (L.direct) {   // first variables of X and Y; tiles 128 or 256 wide
+        g.rowA = g.rowB = 0;
+        g.strideA = g.strideB = 0;
+        bn = bn < kTcBM ? kTcBM : bn;
+    }
     g.k_begin = 0;
     g.k_blocks = static_cast<int32_t>(L.kb);
     g.n_a = static_cast<int32_t>(n1);
@@ -229,13 +283,13 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
         const int bn = rt::choose_bn(m, n1, n2, sym);
         if (path == GBMI_PATH_FUSED)
             return run_gram(c, L.total_rows, tc_job(L, m, n1, n2, sym, bn, va, vb, mp, out, nullptr),
-                            m, kTcModeMI);
+                            m, kTcModeMI, L.direct ? &L.maps : nullptr);
         // plain: exact counts to HBM, then the elementwise MI kernel
         GBMI_TRY(ensure(c.counts, static_cast<size_t>(n1) * n2 * 4, "count matrix"));
         int32_t* N11 = static_cast<int32_t*>(c.counts.p);
         GBMI_TRY(run_gram(c, L.total_rows,
                           tc_job(L, m, n1, n2, sym, bn, va, vb, mp, nullptr, N11), m,
-                          kTcModeCounts));
+                          kTcModeCounts, L.direct ? &L.maps : nullptr));
         GBMI_LAUNCH(launch_mi_from_counts(N11, n2, va, vb, n1, n2, mp, out, n2, g_stream),
                     "mi_from_counts");
         return GBMI_OK;
@@ -313,7 +367,7 @@ gbmi_status counts_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n
     const MiParams mp = rt::mi_params_plain(m, 0, nullptr);
     const int bn = rt::choose_bn(m, n1, n2, sym);
     return run_gram(c, L.total_rows, tc_job(L, m, n1, n2, sym, bn, nullptr, nullptr, mp, nullptr, n11),
-                    m, kTcModeCounts);
+                    m, kTcModeCounts, L.direct ? &L.maps : nullptr);
 }
 
 gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
@@ -341,7 +395,7 @@ gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
     GBMI_CUDA(cudaMemcpy(&err, c.err.p, sizeof(err), cudaMemcpyDeviceToHost), "read error word");
     if (err != 0) {
         cudaMemset(c.err.p, 0, sizeof(err));
-        return fail(GBMI_ERR_TIMEOUT, "a bounded device-side wait timed out");
+        return error_word_status(err);
     }
     return GBMI_OK;
 }
@@ -374,6 +428,10 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
         panel = std::min(panel, std::max<int64_t>(kTcBM, eighth));
     }
     panel = std::min(panel, n1);
+    // direct operands: a panel's first variable is a TMA x coordinate, which
+    // must be a multiple of 16 bytes
+    if (direct_ok(X, Y, n1, n2, sym) && panel % 16 != 0)
+        panel = std::max<int64_t>(16, panel / 16 * 16);
     const int64_t panels = (n1 + panel - 1) / panel;
 
     TcLayout L;
@@ -398,7 +456,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
         std::memset(&g, 0, sizeof(g));
         g.rowA = i0;
         g.strideA = L.rows_a;
-        g.rowB = sym ? i0 : L.kb * L.rows_a;
+        g.rowB = sym ? i0 : (L.direct ? 0 : L.kb * L.rows_a);
         g.strideB = sym ? L.rows_a : L.rows_b;
         g.k_begin = 0;
         g.k_blocks = static_cast<int32_t>(L.kb);
@@ -406,6 +464,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
         g.n_b = static_cast<int32_t>(w);
         g.symmetric = 0;
         g.bn = rt::choose_bn(m, rows, w, false);
+        if (L.direct && g.bn < kTcBM) g.bn = kTcBM;
         g.vec_store = (w % 4 == 0) ? 1 : 0;
         g.va = va + i0;
         g.vb = vb + j0;
@@ -453,7 +512,9 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
                                   cudaMemcpyHostToDevice, g_stream),
                   "tile list upload");
         OperandMaps maps;
-        if (!make_operand_maps(&maps, static_cast<const uint8_t*>(c.P.p), L.total_rows))
+        if (L.direct)
+            maps = L.maps;
+        else if (!make_operand_maps(&maps, static_cast<const uint8_t*>(c.P.p), L.total_rows))
             return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         GBMI_TRY(ensure(c.sched, 256, "tile counter"));
         for (int64_t p = 0; p < panels; ++p) {
@@ -472,6 +533,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
             G.err = static_cast<unsigned int*>(c.err.p);
             G.timeout_ns = g_opt.timeout_ns;
             G.debug_flags = g_opt.debug_flags;
+            G.direct = L.direct ? 1 : 0;
             G.counter = static_cast<unsigned int*>(c.sched.p);
             GBMI_CUDA(cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
             GBMI_LAUNCH(launch_gram_tc(maps, G, rt::grid_for(c, G.num_tiles), g_stream),
@@ -503,7 +565,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
                   "read error word");
         if (err != 0) {
             cudaMemset(c.err.p, 0, sizeof(err));
-            return fail(GBMI_ERR_TIMEOUT, "a bounded device-side wait timed out");
+            return error_word_status(err);
         }
         return GBMI_OK;
     }();
@@ -658,6 +720,9 @@ gbmi_status gbmi_set_option(int option, int64_t value) {
         case GBMI_OPT_PROFILE:
             rt::prof_set(value != 0);
             return GBMI_OK;
+        case GBMI_OPT_DIRECT:
+            g_opt.direct = value != 0 ? 1 : 0;
+            return GBMI_OK;
         case GBMI_OPT_TILE_N:
             if (value != 0 && value != 64 && value != 128 && value != 256)
                 return fail(GBMI_ERR_ARG, "tile width must be 0 (automatic), 64, 128 or 256");
@@ -680,8 +745,7 @@ gbmi_status gbmi_sync(void) {
               "read error word");
     if (err != 0) {
         GBMI_CUDA(cudaMemset(c->err.p, 0, sizeof(err)), "clear error word");
-        return fail(GBMI_ERR_TIMEOUT, "a bounded device-side wait timed out (code " +
-                                          std::to_string(err) + ")");
+        return error_word_status(err);
     }
     return GBMI_OK;
 }

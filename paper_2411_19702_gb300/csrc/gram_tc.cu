@@ -4,7 +4,10 @@
 // Sec. 3.1, with everything after it done per tile while it is on chip).
 //
 // Operands: K-block-major packed matrices (for each block of 128 samples, one
-// 128-byte row per variable, FP8 E4M3 0x00/0x38).  0 and 1 are exact in
+// 128-byte row per variable, FP8 E4M3 0x00/0x38), or, on the direct path, the
+// caller's row-major uint8 0/1 matrix itself read as MN-major E4M3 (a byte 1
+// is the subnormal 2^-9; counts come out scaled by 2^-18, still exact; the
+// epilogue scales them back).  0 and 1 are exact in
 // E4M3, every product is 0 or 1 and the FP32 accumulator holds integers
 // exactly below 2^24, so a tile's counts are exact as long as one launch
 // accumulates at most 2^24 samples (k_blocks * 128).  One launch can serve
@@ -160,6 +163,13 @@ __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const Gram
         const uint32_t bytes = static_cast<uint32_t>((kTcBM + bn) * kTcBK);
         const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * kTcBM;
         const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn;
+        if (L.direct && ((a0 | b0) & 15) != 0) {
+            // a direct copy's x coordinate (a variable index) must be a multiple
+            // of 16 bytes: record it and issue nothing
+            raise_abort(sm, L.err, kErrBadOperand);
+            ok = false;
+            break;
+        }
         for (int kb = 0; kb < job.k_blocks; ++kb) {
             if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, L.timeout_ns,
                                         sm.abort_flag())) {
@@ -169,10 +179,20 @@ __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const Gram
             }
             const int64_t k = job.k_begin + kb;
             ptx::mbar_arrive_expect_tx(sm.full(stage), bytes);
-            ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.box128, sm.full(stage), 0,
-                             static_cast<int32_t>(a0 + k * job.strideA));
-            ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), mapB, sm.full(stage), 0,
-                             static_cast<int32_t>(b0 + k * job.strideB));
+            if (L.direct) {
+                // 128 variables x 128 samples of X per box; B in bn / 128 boxes
+                const int32_t y = static_cast<int32_t>(k * kTcBK);
+                ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.xa, sm.full(stage),
+                                 static_cast<int32_t>(a0), y);
+                for (int h = 0; h < bn; h += kTcBM)
+                    ptx::tma_load_2d(ptx::smem_u32(sm.b(stage) + h * kTcBK), &maps.xb,
+                                     sm.full(stage), static_cast<int32_t>(b0 + h), y);
+            } else {
+                ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.box128, sm.full(stage), 0,
+                                 static_cast<int32_t>(a0 + k * job.strideA));
+                ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), mapB, sm.full(stage), 0,
+                                 static_cast<int32_t>(b0 + k * job.strideB));
+            }
             pending_parity[stage] = static_cast<int>(phase);
             if (++stage == kStages) {
                 stage = 0;
@@ -221,7 +241,9 @@ __device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base)
         if (t < 0) break;
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
-        const uint32_t idesc = ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(job.bn));
+        const uint32_t idesc =
+            L.direct ? ptx::idesc_e4m3_f32_mnmajor(kTcBM, static_cast<uint32_t>(job.bn))
+                     : ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(job.bn));
         const int k_blocks = job.k_blocks;
         if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, L.timeout_ns,
                                     sm.abort_flag())) {
@@ -237,14 +259,29 @@ __device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base)
                 break;
             }
             ptx::tc_fence_after();
-            const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
-            const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
+            if (L.direct) {
+                // MN-major: 128-sample K-rows of 128 bytes, 128-variable atoms of
+                // B 16 KB apart; K step kk starts kk * 32 rows (4 atoms) further
+                const uint64_t adesc =
+                    ptx::smem_desc_mnmajor_sw128(ptx::smem_u32(sm.a(stage)), kTcBM * kTcBK);
+                const uint64_t bdesc =
+                    ptx::smem_desc_mnmajor_sw128(ptx::smem_u32(sm.b(stage)), kTcBM * kTcBK);
 #pragma unroll
-            for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
-                // advance the start address by kk * 32 bytes inside the swizzle row
-                const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
-                ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
-                                (kb | kk) != 0 ? 1u : 0u);
+                for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                    const uint64_t off = static_cast<uint64_t>((kk * kUmmaK * kTcBK) >> 4);
+                    ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
+                                    (kb | kk) != 0 ? 1u : 0u);
+                }
+            } else {
+                const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
+                const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
+#pragma unroll
+                for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                    // advance the start address by kk * 32 bytes inside the swizzle row
+                    const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+                    ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
+                                    (kb | kk) != 0 ? 1u : 0u);
+                }
             }
             ptx::mma_commit(sm.empty(stage));   // frees the slot when these MMAs finish
             if (++stage == kStages) {
@@ -290,6 +327,7 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
     const int lane_base = (warp & 3) * 32;             // TMEM lanes this warp may access
     const int half = (warp - 2) >> 2;                  // which half of the tile's columns
     MiVar* cv = sm.colvars(warp - 2);                  // this warp's column terms
+    const float cscale = L.direct ? 262144.f : 1.f;    // 2^18: direct operands hold 2^-9
     int acc = 0;
     uint32_t acc_phase = 0;
     int qslot = 0;
@@ -361,7 +399,7 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q) {
                     const int64_t j = j0 + q;
-                    const int32_t n11 = __float2int_rn(__uint_as_float(r[q]));
+                    const int32_t n11 = __float2int_rn(__uint_as_float(r[q]) * cscale);
                     float mi = 0.f;
                     if (row_ok && j < n_b && (!sym || j >= i)) {
                         const MiVar B = cv[g + q];
@@ -413,7 +451,7 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
             } else {
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q)
-                    r[q] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[q])));
+                    r[q] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[q]) * cscale));
             }
             // (j, i): lanes hold consecutive i -> each store is one coalesced row segment
             if (sym && row_ok) {
@@ -506,9 +544,14 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
         ptx::fence_barrier_init();
     }
     if (warp == 0 && lane == 0) {
-        ptx::tma_prefetch_desc(&maps.box64);
-        ptx::tma_prefetch_desc(&maps.box128);
-        ptx::tma_prefetch_desc(&maps.box256);
+        if (L.direct) {
+            ptx::tma_prefetch_desc(&maps.xa);
+            ptx::tma_prefetch_desc(&maps.xb);
+        } else {
+            ptx::tma_prefetch_desc(&maps.box64);
+            ptx::tma_prefetch_desc(&maps.box128);
+            ptx::tma_prefetch_desc(&maps.box256);
+        }
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(sm.tmem_holder()), kTmemCols);

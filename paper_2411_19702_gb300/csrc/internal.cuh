@@ -37,6 +37,8 @@ enum : uint32_t {
     kErrTimeoutMma = 2u,
     kErrTimeoutEpilogue = 4u,
     kErrTimeoutDrain = 8u,
+    kErrNotBinary = 16u,     // the direct operand path met a byte other than 0 / 1
+    kErrBadOperand = 32u,    // a direct operand tile did not start on a 16-byte boundary
 };
 
 // -------------------------------------------------------------- pack kernel
@@ -60,6 +62,11 @@ cudaError_t launch_pack_grouped(const PackJob* jobs, int njobs, int64_t total_ct
                                 cudaStream_t s);
 cudaError_t launch_validate(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
                             unsigned int* flag, cudaStream_t s);
+// Column counts of X for the direct operand path (n % 16 == 0, X 16-byte
+// aligned): v[j] += sum_r X[r][j] (v zeroed before); a byte other than 0 / 1
+// sets kErrNotBinary in *err.
+cudaError_t launch_colsum_direct(const uint8_t* X, int64_t m, int64_t n, int32_t* v,
+                                 unsigned int* err, int sm_count, cudaStream_t s);
 
 // ----------------------------------------------------- elementwise kernels
 cudaError_t launch_zero_u32(void* p, int64_t words, cudaStream_t s);
@@ -133,6 +140,13 @@ struct GramLaunch {
     unsigned int* err;
     uint64_t timeout_ns;
     int debug_flags;
+    // Operands: 0 = packed K-block-major FP8 buffer (box64/128/256, rowA/rowB
+    // are buffer rows); 1 = direct: the caller's uint8 0/1 matrices read as
+    // MN-major E4M3 through xa / xb (rowA/rowB are first variables, bn is 128
+    // or 256, k_blocks count 128-sample steps).  A byte 1 is the E4M3
+    // subnormal 2^-9, so the accumulator holds count * 2^-18 (exact below 2^24
+    // samples) and the epilogue scales it back by 2^18.
+    int direct;
     // Dynamic tile order: CTAs take the next tile from this counter (zero at
     // launch), so the tiles in flight are always a contiguous window of the
     // list.  Null: static round-robin (tile blockIdx.x + k * gridDim.x).
@@ -143,8 +157,15 @@ struct GramLaunch {
 // bytes, for boxes of 64, 128 and 256 rows (128-byte swizzle).
 struct OperandMaps {
     CUtensorMap box64, box128, box256;
+    // direct operands: X (A) and Y or X (B) themselves, row-major samples x
+    // variables, boxes of 128 variables x 128 samples (128-byte swizzle)
+    CUtensorMap xa, xb;
 };
 bool make_operand_maps(OperandMaps* maps, const uint8_t* P, int64_t total_rows);
+// Direct-operand maps over X (m x n1) and Y (m x n2; Y = X for all pairs).
+// Needs n1, n2 multiples of 16 and 16-byte aligned X, Y.
+bool make_direct_maps(OperandMaps* maps, const uint8_t* X, int64_t m, int64_t n1,
+                      const uint8_t* Y, int64_t n2);
 // Tiles of one job in the kernel's order (groups of group_cols column blocks).
 int64_t gram_tile_count(int64_t n_a, int64_t n_b, int bn, bool symmetric);
 void gram_tiles(int job, int64_t n_a, int64_t n_b, int bn, bool symmetric, int group_cols,

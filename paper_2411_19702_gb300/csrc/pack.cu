@@ -221,6 +221,74 @@ __global__ void validate_kernel(const uint8_t* X, int64_t m, int64_t n, int64_t 
     }
 }
 
+// Column counts for the direct operand path, which feeds the caller's X to the
+// tensor cores without packing (n a multiple of 16, X 16-byte aligned): a
+// block owns 512 columns (a warp reads 512 contiguous bytes of one row, one
+// 16-byte load per lane) and a slice of rows split over its 8 warps.  Bytes
+// are summed in 16-bit lanes (two per register, flushed every 255 rows, so
+// any byte value is summed exactly), the warps' sums meet in shared memory
+// and each column gets one atomic add per block.  A byte other than 0 / 1
+// sets kErrNotBinary: the direct Gram reads bytes as E4M3 values, so
+// non-binary data would not count as 1.
+constexpr int kCsCols = 512;
+constexpr int kCsWarps = 8;
+
+__global__ void __launch_bounds__(kCsWarps * 32)
+colsum_kernel(const uint8_t* __restrict__ X, int64_t m, int64_t n, int64_t rows_per_block,
+              int32_t* __restrict__ v, unsigned int* err) {
+    __shared__ int32_t red[kCsWarps][kCsCols + 16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kCsCols + lane * 16;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows_per_block;
+    const int64_t r1 = r0 + rows_per_block < m ? r0 + rows_per_block : m;
+    int32_t tot[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) tot[k] = 0;
+    uint32_t acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0;
+    uint32_t bad = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            tot[4 * q + 0] += static_cast<int32_t>(acc[2 * q] & 0xFFFFu);
+            tot[4 * q + 2] += static_cast<int32_t>(acc[2 * q] >> 16);
+            tot[4 * q + 1] += static_cast<int32_t>(acc[2 * q + 1] & 0xFFFFu);
+            tot[4 * q + 3] += static_cast<int32_t>(acc[2 * q + 1] >> 16);
+            acc[2 * q] = acc[2 * q + 1] = 0;
+        }
+    };
+    if (c0 < n) {   // n % 16 == 0: the lane's 16 bytes are inside the row
+        int it = 0;
+        for (int64_t r = r0 + w; r < r1; r += kCsWarps) {
+            const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(X + r * n + c0));
+            const uint32_t ws[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                bad |= ws[q] & 0xFEFEFEFEu;
+                acc[2 * q] += ws[q] & 0x00FF00FFu;
+                acc[2 * q + 1] += (ws[q] >> 8) & 0x00FF00FFu;
+            }
+            if (++it == 255) {
+                flush();
+                it = 0;
+            }
+        }
+        flush();
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) red[w][lane * 16 + k] = tot[k];
+    if (__any_sync(0xffffffffu, bad != 0) && lane == 0) atomicOr(err, kErrNotBinary);
+    __syncthreads();
+    for (int c = threadIdx.x; c < kCsCols; c += kCsWarps * 32) {
+        int32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < kCsWarps; ++k) sum += red[k][c];
+        const int64_t col = static_cast<int64_t>(blockIdx.x) * kCsCols + c;
+        if (col < n && sum != 0) atomicAdd(v + col, sum);
+    }
+}
+
 }  // namespace
 
 int64_t pack_job_ctas(PackJob& a) {
@@ -255,6 +323,23 @@ cudaError_t launch_pack_grouped(const PackJob* jobs, int njobs, int64_t total_ct
 cudaError_t launch_validate(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
                             unsigned int* flag, cudaStream_t s) {
     validate_kernel<<<1024, 256, 0, s>>>(X, m, n, ldx, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colsum_direct(const uint8_t* X, int64_t m, int64_t n, int32_t* v,
+                                 unsigned int* err, int sm_count, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (n % 16 != 0 || (reinterpret_cast<uintptr_t>(X) & 15u) != 0) return cudaErrorInvalidValue;
+    const int64_t gx = (n + kCsCols - 1) / kCsCols;
+    const int64_t want = static_cast<int64_t>(sm_count > 0 ? sm_count : 152) * 8;
+    int64_t gy = (want + gx - 1) / gx;
+    gy = gy < 1 ? 1 : gy;
+    int64_t rows = (m + gy - 1) / gy;
+    rows = (rows + kCsWarps - 1) / kCsWarps * kCsWarps;
+    gy = (m + rows - 1) / rows;
+    if (gx > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidValue;
+    colsum_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy)), kCsWarps * 32, 0,
+                    s>>>(X, m, n, rows, v, err);
     return cudaGetLastError();
 }
 

@@ -144,6 +144,24 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor_sw128(uint32_t smem_addr) {
     return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major operand tile stored with the
+// 128-byte swizzle: each 1024-byte atom holds 8 K-rows of 128 bytes (128
+// consecutive 8-bit elements along M or N); atoms of consecutive K-row groups
+// are 1024 bytes apart (stride-dimension offset) and atoms of consecutive
+// 128-element groups along M/N are mn_atom_bytes apart (leading-dimension
+// offset).  This is the layout a TMA box of 128 bytes x K rows writes with
+// CU_TENSOR_MAP_SWIZZLE_128B from a row-major (K rows of M/N elements) matrix.
+__device__ __forceinline__ uint64_t smem_desc_mnmajor_sw128(uint32_t smem_addr,
+                                                           uint32_t mn_atom_bytes) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((smem_addr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>((mn_atom_bytes >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>(1024u >> 4) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(2u) << 61;
+    return d;
+}
+
 // Instruction descriptor for tcgen05.mma kind::f8f6f4 with E4M3 A and B, FP32
 // accumulation, both operands K-major, shape M x N.
 //   bits 4-5 D format (1 = F32), bits 7-9 A format (0 = E4M3), bits 10-12 B
@@ -151,6 +169,11 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor_sw128(uint32_t smem_addr) {
 //   bits 24-28 M >> 4.
 __host__ __device__ constexpr uint32_t idesc_e4m3_f32(uint32_t M, uint32_t N) {
     return (1u << 4) | (0u << 7) | (0u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// The same with both operands MN-major (bits 15 and 16 set).
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32_mnmajor(uint32_t M, uint32_t N) {
+    return idesc_e4m3_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.

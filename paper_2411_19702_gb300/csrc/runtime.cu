@@ -279,9 +279,29 @@ bool encode_box(CUtensorMap* tm, const uint8_t* P, int64_t total_rows, int box_r
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
 }
+// A row-major m x n uint8 matrix as a 2-D tensor (x = variable, y = sample)
+// with boxes of 128 variables x 128 samples.
+bool encode_direct(CUtensorMap* tm, const uint8_t* X, int64_t m, int64_t n) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (fn == nullptr || n % 16 != 0 || (reinterpret_cast<uintptr_t>(X) & 15u) != 0) return false;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(m)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(n)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kTcBM), static_cast<cuuint32_t>(kTcBK)};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(X), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
 }  // namespace
 
 const char* last_error_text() { return t_last_error.c_str(); }
+
+bool make_direct_maps(OperandMaps* maps, const uint8_t* X, int64_t m, int64_t n1,
+                      const uint8_t* Y, int64_t n2) {
+    if (m <= 0 || m >= (int64_t{1} << 31)) return false;
+    return encode_direct(&maps->xa, X, m, n1) && encode_direct(&maps->xb, Y, m, n2);
+}
 
 bool make_operand_maps(OperandMaps* maps, const uint8_t* P, int64_t total_rows) {
     if (total_rows <= 0 || total_rows >= (int64_t{1} << 31)) return false;

@@ -29,6 +29,7 @@ struct Options {
     int group_cols = 8;
     int max_ctas = 0;
     int tile_n = 0;                      // 0: tuner table / cost model; else forced 64/128/256
+    int direct = 0;                      // 1: no pack where X's rows are 16-byte multiples
 };
 
 struct DeviceCtx {
