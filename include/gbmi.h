@@ -69,11 +69,17 @@ typedef enum {
     GBMI_OPT_MAX_CTAS = 5,       /* cap on persistent CTAs, 0 = one per SM (default 0)           */
     GBMI_OPT_PROFILE = 6,        /* 1: time every kernel launch with CUDA events (default 0)     */
     GBMI_OPT_TILE_N = 7,         /* tensor-core tile width 64/128/256; 0 = tuner / model (default) */
-    GBMI_OPT_DIRECT = 8          /* 1: tensor-core paths read X / Y directly, without the pack pass
+    GBMI_OPT_DIRECT = 8,         /* 1: tensor-core paths read X / Y directly, without the pack pass
                                     or its packed copy, when n (and n2) are multiples of 16 and X, Y
                                     are 16-byte aligned; bytes must then be 0 / 1 (others are
                                     reported as GBMI_ERR_NOT_BINARY by gbmi_sync).  Saves m*n bytes
                                     of device memory but measured slower (default 0)          */
+    GBMI_OPT_PAIR = 9            /* 1: the single-call and out-of-core tensor-core paths run the
+                                    Gram on CTA pairs (clusters of two SMs sharing one tcgen05
+                                    cta_group::2 MMA of 256 x 256 x 32; each SM stages half of A
+                                    and half of B) whenever that keeps at least as many SMs busy as
+                                    single-CTA tiles would; 2: always; 0: single-CTA tiles only
+                                    (default 1)                                                  */
 } gbmi_option;
 
 /* ---------------------------------------------------------------- core calls */

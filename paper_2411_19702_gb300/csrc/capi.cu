@@ -77,14 +77,15 @@ gbmi_status mi_vars(const int32_t* v, int64_t n, const MiParams& P, DevBuf& out,
 }
 
 // Tile list of one job (cached per shape), uploaded to the workspace.
-gbmi_status tile_list(DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn, int* count) {
+gbmi_status tile_list(DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn, int* count,
+                      int bm = kTcBM) {
     const int group = std::max(1, g_opt.group_cols);
     if (!(c.tl_na == n_a && c.tl_nb == n_b && c.tl_sym == (int)sym && c.tl_group == group &&
-          c.tl_bn == bn)) {
-        const int64_t k = gram_tile_count(n_a, n_b, bn, sym);
+          c.tl_bn == bn && c.tl_bm == bm)) {
+        const int64_t k = gram_tile_count(n_a, n_b, bn, sym, bm);
         if (k > 0x7FFFFFFF) return fail(GBMI_ERR_ARG, "too many tiles");
         std::vector<GramTile> list(static_cast<size_t>(k));
-        gram_tiles(0, n_a, n_b, bn, sym, group, list.data());
+        gram_tiles(0, n_a, n_b, bn, sym, group, list.data(), bm);
         GBMI_TRY(ensure(c.tiles, list.size() * sizeof(GramTile), "tile list"));
         c.tl_host.swap(list);
         GBMI_CUDA(cudaMemcpyAsync(c.tiles.p, c.tl_host.data(),
@@ -96,9 +97,23 @@ gbmi_status tile_list(DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn, 
         c.tl_sym = sym;
         c.tl_group = group;
         c.tl_bn = bn;
+        c.tl_bm = bm;
     }
     *count = static_cast<int>(c.tl_host.size());
     return GBMI_OK;
+}
+
+// The CTA-pair kernel streams half the operand bytes per SM per MMA, so it is
+// taken whenever its launch keeps at least as many SMs busy as the single-CTA
+// launch of the same problem would (small problems keep the finer tiles).
+bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn) {
+    if (g_opt.pair == 0 || c.pair_clusters <= 0) return false;
+    if (g_opt.pair == 2) return true;   // forced (tests)
+    if (g_opt.tile_n != 0) return false;   // a forced tile width names a single-CTA tile
+    const int64_t pair_tiles = gram_tile_count(n_a, n_b, kTcBNMax, sym, 2 * kTcBM);
+    const int64_t single_tiles = gram_tile_count(n_a, n_b, bn, sym, kTcBM);
+    const int64_t pair_sms = 2 * std::min<int64_t>(pair_tiles, c.pair_clusters);
+    return pair_sms >= std::min<int64_t>(single_tiles, c.sm_count);
 }
 
 // Run the tensor-core Gram of one job over [0, m) in exact chunks.  mode MI
@@ -111,12 +126,19 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
         maps = *dmaps;
     else if (!make_operand_maps(&maps, static_cast<const uint8_t*>(c.P.p), total_rows))
         return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    // CTA pairs: 256 x 256 tiles on clusters of two SMs (packed operands only)
+    const bool pair = dmaps == nullptr &&
+                      use_pair(c, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn);
+    const int bn = pair ? kTcBNMax : proto.bn;
+    const int bm = pair ? 2 * kTcBM : kTcBM;
     int tiles = 0;
-    GBMI_TRY(tile_list(c, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn, &tiles));
+    GBMI_TRY(tile_list(c, proto.n_a, proto.n_b, proto.symmetric != 0, bn, &tiles, bm));
     GramLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.jobs = nullptr;
     L.job0 = proto;
+    L.job0.bn = bn;
+    L.pair = pair ? 1 : 0;
     L.tiles = static_cast<const GramTile*>(c.tiles.p);
     L.num_tiles = tiles;
     L.err = static_cast<unsigned int*>(c.err.p);
@@ -129,7 +151,8 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     const int64_t kb_chunk = kExactChunk / kTcBK;
     if (mode == kTcModeMI && kb_total > kb_chunk)
         return fail(GBMI_ERR_ARG, "fused path needs m <= 2^24");
-    const int grid = rt::grid_for(c, tiles);
+    const int grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, tiles))
+                          : rt::grid_for(c, tiles);
     for (int64_t k0 = 0; k0 < kb_total; k0 += kb_chunk) {
         L.job0.k_begin = static_cast<int32_t>(k0);
         L.job0.k_blocks = static_cast<int32_t>(std::min(kb_chunk, kb_total - k0));
@@ -449,6 +472,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
     const int group = std::max(1, g_opt.group_cols);
     std::vector<GramJob> jobs(static_cast<size_t>(panels));
     std::vector<int64_t> first(static_cast<size_t>(panels) + 1, 0);
+    std::vector<char> pair_panel(static_cast<size_t>(panels), 0);
     for (int64_t p = 0; p < panels; ++p) {
         const int64_t i0 = p * panel, rows = std::min(panel, n1 - i0);
         const int64_t j0 = sym ? i0 : 0, w = n2 - j0;
@@ -465,21 +489,27 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
         g.symmetric = 0;
         g.bn = rt::choose_bn(m, rows, w, false);
         if (L.direct && g.bn < kTcBM) g.bn = kTcBM;
+        if (!L.direct && use_pair(c, rows, w, false, g.bn)) {
+            g.bn = kTcBNMax;
+            pair_panel[static_cast<size_t>(p)] = 1;
+        }
         g.vec_store = (w % 4 == 0) ? 1 : 0;
         g.va = va + i0;
         g.vb = vb + j0;
         g.ld_out = w;
         g.ld_t = rows;
         g.mp = mp;
-        first[static_cast<size_t>(p) + 1] = first[static_cast<size_t>(p)] +
-                                            gram_tile_count(rows, w, g.bn, false);
+        first[static_cast<size_t>(p) + 1] =
+            first[static_cast<size_t>(p)] +
+            gram_tile_count(rows, w, g.bn, false, pair_panel[p] ? 2 * kTcBM : kTcBM);
     }
     const int64_t total_tiles = first.back();
     std::vector<GramTile> tiles(static_cast<size_t>(total_tiles));
     for (int64_t p = 0; p < panels; ++p) {
         const GramJob& g = jobs[static_cast<size_t>(p)];
         if (first[p + 1] - first[p] > 0x7FFFFFFF) return fail(GBMI_ERR_ARG, "too many tiles");
-        gram_tiles(0, g.n_a, g.n_b, g.bn, false, group, tiles.data() + first[p]);
+        gram_tiles(0, g.n_a, g.n_b, g.bn, false, group, tiles.data() + first[p],
+                   pair_panel[p] ? 2 * kTcBM : kTcBM);
     }
 
     const size_t up_bytes = static_cast<size_t>(panel) * n2 * 4;
@@ -534,10 +564,13 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
             G.timeout_ns = g_opt.timeout_ns;
             G.debug_flags = g_opt.debug_flags;
             G.direct = L.direct ? 1 : 0;
+            G.pair = pair_panel[p];
             G.counter = static_cast<unsigned int*>(c.sched.p);
+            const int grid =
+                G.pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, G.num_tiles))
+                       : rt::grid_for(c, G.num_tiles);
             GBMI_CUDA(cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
-            GBMI_LAUNCH(launch_gram_tc(maps, G, rt::grid_for(c, G.num_tiles), g_stream),
-                        "gram_tc_fused_mi");
+            GBMI_LAUNCH(launch_gram_tc(maps, G, grid, g_stream), "gram_tc_fused_mi");
             GBMI_CUDA(cudaEventRecord(computed[s], g_stream), "event");
             GBMI_CUDA(cudaStreamWaitEvent(cs, computed[s], 0), "wait panel");
             if (sym) {
@@ -722,6 +755,10 @@ gbmi_status gbmi_set_option(int option, int64_t value) {
             return GBMI_OK;
         case GBMI_OPT_DIRECT:
             g_opt.direct = value != 0 ? 1 : 0;
+            return GBMI_OK;
+        case GBMI_OPT_PAIR:
+            if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "pair mode must be 0, 1 or 2");
+            g_opt.pair = static_cast<int>(value);
             return GBMI_OK;
         case GBMI_OPT_TILE_N:
             if (value != 0 && value != 64 && value != 128 && value != 256)

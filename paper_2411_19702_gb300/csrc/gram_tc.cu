@@ -47,6 +47,7 @@
 // waits (bounded) for its copies still in flight, the MMA thread for its
 // MMAs, and warp 1 frees the tensor memory before the CTA exits.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.cuh"
 #include "ptx.cuh"
@@ -55,63 +56,79 @@ namespace gbmi {
 
 namespace {
 
-constexpr int kStages = 4;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;    // 320
 constexpr int kUmmaK = 32;                       // K per MMA for 8-bit inputs
-constexpr int kABytes = kTcBM * kTcBK;           // 16 KB
-constexpr int kBBytes = kTcBNMax * kTcBK;        // 32 KB (room for the widest tile)
-constexpr int kStageBytes = kABytes + kBBytes;   // 48 KB
+constexpr int kABytes = kTcBM * kTcBK;           // 16 KB: 128 rows of A
 constexpr int kAccCols = kTcBNMax;               // TMEM columns per accumulator buffer
 constexpr int kTmemCols = 2 * kAccCols;          // 512: the whole tensor memory
 constexpr int kColsPerWarpMax = kTcBNMax / 2;    // 128
 constexpr int kGroup = 16;                       // accumulator columns per tcgen05.ld
-
-constexpr size_t kOffStages = 0;
-constexpr size_t kOffColVars = kOffStages + static_cast<size_t>(kStages) * kStageBytes;
-constexpr size_t kColVarBytes = static_cast<size_t>(kColsPerWarpMax) * sizeof(MiVar);   // 4 KB
 constexpr int kQ = 8;                            // tile-id queue between the roles
-constexpr size_t kOffBars = kOffColVars + kEpiWarps * kColVarBytes;
+constexpr size_t kColVarBytes = static_cast<size_t>(kColsPerWarpMax) * sizeof(MiVar);   // 4 KB
 // full, empty, tmem full x2, tmem empty x2, drain, queue full x kQ, queue empty x kQ
-constexpr int kNumBars = 2 * kStages + 4 + 1 + 2 * kQ;
-constexpr size_t kOffMisc = kOffBars + kNumBars * 8;
-constexpr size_t kOffQueue = kOffMisc + 64;
-constexpr size_t kSmemBytes = 1024 + kOffQueue + kQ * 4;
+constexpr int kNumBarsFor(int stages) { return 2 * stages + 4 + 1 + 2 * kQ; }
 
-static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte alignment");
-static_assert(kSmemBytes <= 232448, "shared memory budget");
+// Shared-memory plan.  Single CTA: 4 stages of A (128 rows) + B (up to 256
+// rows).  CTA pair: 6 stages of this CTA's halves, 128 rows of A and 128 rows
+// of B (the pair's tile is 256 x 256).
+template <bool kPair>
+struct Plan {
+    static constexpr int stages = kPair ? 6 : 4;
+    static constexpr int b_bytes = kPair ? kTcBM * kTcBK : kTcBNMax * kTcBK;
+    static constexpr int stage_bytes = kABytes + b_bytes;
+    static constexpr int tile_m = kPair ? 2 * kTcBM : kTcBM;   // rows of A per tile
+    static constexpr size_t off_colvars = static_cast<size_t>(stages) * stage_bytes;
+    static constexpr size_t off_bars = off_colvars + kEpiWarps * kColVarBytes;
+    static constexpr int num_bars = kNumBarsFor(stages);
+    static constexpr size_t off_misc = off_bars + num_bars * 8;
+    static constexpr size_t off_queue = off_misc + 64;
+    static constexpr size_t smem_bytes = 1024 + off_queue + kQ * 4;
+    static_assert(stage_bytes % 1024 == 0, "stages must keep 1024-byte alignment");
+    static_assert(smem_bytes <= 232448, "shared memory budget");
+};
 
+template <bool kPair>
 struct Smem {
+    using P = Plan<kPair>;
     uint8_t* base;
-    __device__ uint8_t* a(int s) const { return base + kOffStages + s * kStageBytes; }
-    __device__ uint8_t* b(int s) const { return base + kOffStages + s * kStageBytes + kABytes; }
+    uint32_t rank;   // CTA rank in the pair (0 when single)
+    __device__ uint8_t* a(int s) const { return base + s * P::stage_bytes; }
+    __device__ uint8_t* b(int s) const { return base + s * P::stage_bytes + kABytes; }
     __device__ MiVar* colvars(int e) const {
-        return reinterpret_cast<MiVar*>(base + kOffColVars + e * kColVarBytes);
+        return reinterpret_cast<MiVar*>(base + P::off_colvars + e * kColVarBytes);
     }
-    __device__ uint64_t* bar(int k) const { return reinterpret_cast<uint64_t*>(base + kOffBars) + k; }
+    __device__ uint64_t* bar(int k) const {
+        return reinterpret_cast<uint64_t*>(base + P::off_bars) + k;
+    }
     __device__ uint32_t full(int s) const { return ptx::smem_u32(bar(s)); }
-    __device__ uint32_t empty(int s) const { return ptx::smem_u32(bar(kStages + s)); }
-    __device__ uint32_t tfull(int b) const { return ptx::smem_u32(bar(2 * kStages + b)); }
-    __device__ uint32_t tempty(int b) const { return ptx::smem_u32(bar(2 * kStages + 2 + b)); }
-    __device__ uint32_t drain() const { return ptx::smem_u32(bar(2 * kStages + 4)); }
-    __device__ uint32_t qfull(int q) const { return ptx::smem_u32(bar(2 * kStages + 5 + q)); }
+    __device__ uint32_t empty(int s) const { return ptx::smem_u32(bar(P::stages + s)); }
+    __device__ uint32_t tfull(int b) const { return ptx::smem_u32(bar(2 * P::stages + b)); }
+    __device__ uint32_t tempty(int b) const { return ptx::smem_u32(bar(2 * P::stages + 2 + b)); }
+    __device__ uint32_t drain() const { return ptx::smem_u32(bar(2 * P::stages + 4)); }
+    __device__ uint32_t qfull(int q) const { return ptx::smem_u32(bar(2 * P::stages + 5 + q)); }
     __device__ uint32_t qempty(int q) const {
-        return ptx::smem_u32(bar(2 * kStages + 5 + kQ + q));
+        return ptx::smem_u32(bar(2 * P::stages + 5 + kQ + q));
     }
     __device__ volatile int* queue() const {
-        return reinterpret_cast<volatile int*>(base + kOffQueue);
+        return reinterpret_cast<volatile int*>(base + P::off_queue);
     }
     __device__ uint32_t* tmem_holder() const {
-        return reinterpret_cast<uint32_t*>(base + kOffMisc);
+        return reinterpret_cast<uint32_t*>(base + P::off_misc);
     }
     __device__ volatile int* abort_flag() const {
-        return reinterpret_cast<volatile int*>(base + kOffMisc + 4);
+        return reinterpret_cast<volatile int*>(base + P::off_misc + 4);
     }
 };
 
-__device__ __forceinline__ void raise_abort(const Smem& sm, unsigned int* err, uint32_t code) {
+template <bool kPair>
+__device__ __forceinline__ void raise_abort(const Smem<kPair>& sm, unsigned int* err,
+                                            uint32_t code) {
     atomicOr(err, code);
     *sm.abort_flag() = 1;
+    if constexpr (kPair)   // the partner CTA unwinds too
+        ptx::st_cluster_u32(
+            ptx::mapa_shared(ptx::smem_u32(const_cast<int*>(sm.abort_flag())), sm.rank ^ 1u), 1u);
 }
 
 __device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
@@ -121,12 +138,44 @@ __device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
 // ------------------------------------------------------------------ producer
 // Next tile of this CTA: from the shared counter (dynamic order) or the static
 // round-robin sequence.
+// A CTA pair takes the static sequence of its cluster (both CTAs see the same).
+template <bool kPair>
 __device__ __forceinline__ int next_tile(const GramLaunch& L, int s) {
-    if (L.counter != nullptr) return static_cast<int>(atomicAdd(L.counter, 1u));
-    return blockIdx.x + s * gridDim.x;
+    if constexpr (kPair) {
+        return static_cast<int>(ptx::cluster_id_x() + s * ptx::nclusters_x());
+    } else {
+        if (L.counter != nullptr) return static_cast<int>(atomicAdd(L.counter, 1u));
+        return blockIdx.x + s * gridDim.x;
+    }
 }
 
-__device__ void run_producer(const Smem& sm, const OperandMaps& maps, const GramLaunch& L) {
+// Second CTA of a pair: no copies (CTA 0 loads both CTAs' halves), only the
+// tile ids for its own epilogue warps.
+__device__ void run_feeder(const Smem<true>& sm, const GramLaunch& L) {
+    int qslot = 0;
+    uint32_t qphase = 0;
+    for (int s = 0;; ++s) {
+        const int t = next_tile<true>(L, s);
+        if (!ptx::mbar_wait_bounded(sm.qempty(qslot), qphase ^ 1u, L.timeout_ns,
+                                    sm.abort_flag())) {
+            raise_abort(sm, L.err, kErrTimeoutLoad);
+            break;
+        }
+        const int tid = t < L.num_tiles ? t : -1;
+        sm.queue()[qslot] = tid;
+        ptx::mbar_arrive(sm.qfull(qslot));
+        if (++qslot == kQ) {
+            qslot = 0;
+            qphase ^= 1u;
+        }
+        if (tid < 0) break;
+    }
+}
+
+template <bool kPair>
+__device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
+                             const GramLaunch& L) {
+    constexpr int kStages = Plan<kPair>::stages;
     int pending_parity[kStages];
 #pragma unroll
     for (int s = 0; s < kStages; ++s) pending_parity[s] = -1;
@@ -136,7 +185,7 @@ __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const Gram
     uint32_t qphase = 0;
     bool ok = true;
     int s = 0;
-    int t = next_tile(L, 0);
+    int t = next_tile<kPair>(L, 0);
     while (ok) {
         // publish the tile id (-1 at the end) to the MMA thread and the epilogue
         if (!ptx::mbar_wait_bounded(sm.qempty(qslot), qphase ^ 1u, L.timeout_ns,
@@ -154,14 +203,14 @@ __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const Gram
         }
         if (tid < 0) break;
         if (L.debug_flags & 1) break;   // test hook: issue no copies, consumers must time out
-        const int t_next = next_tile(L, ++s);   // its latency overlaps this tile's copies
+        const int t_next = next_tile<kPair>(L, ++s);   // its latency overlaps this tile's copies
         const GramTile tile = L.tiles[tid];
         const GramJob& job = job_of(L, tile.job);
         const int bn = job.bn;
         const CUtensorMap* mapB = bn == 256 ? &maps.box256 : (bn == 128 ? &maps.box128
                                                                          : &maps.box64);
-        const uint32_t bytes = static_cast<uint32_t>((kTcBM + bn) * kTcBK);
-        const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * kTcBM;
+        const uint32_t bytes = static_cast<uint32_t>((Plan<kPair>::tile_m + bn) * kTcBK);
+        const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m;
         const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn;
         if (L.direct && ((a0 | b0) & 15) != 0) {
             // a direct copy's x coordinate (a variable index) must be a multiple
@@ -179,7 +228,18 @@ __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const Gram
             }
             const int64_t k = job.k_begin + kb;
             ptx::mbar_arrive_expect_tx(sm.full(stage), bytes);
-            if (L.direct) {
+            if constexpr (kPair) {
+                // CTA 0 loads both CTAs' halves (rows +0 and +128 of A and of B);
+                // every copy completes on CTA 0's full barrier
+                const int32_t ya = static_cast<int32_t>(a0 + k * job.strideA);
+                const int32_t yb = static_cast<int32_t>(b0 + k * job.strideB);
+                ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.box128, sm.full(stage), 0, ya);
+                ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), &maps.box128, sm.full(stage), 0, yb);
+                ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.a(stage)), 1u),
+                                      &maps.box128, sm.full(stage), 0, ya + kTcBM);
+                ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.b(stage)), 1u),
+                                      &maps.box128, sm.full(stage), 0, yb + kTcBM);
+            } else if (L.direct) {
                 // 128 variables x 128 samples of X per box; B in bn / 128 boxes
                 const int32_t y = static_cast<int32_t>(k * kTcBK);
                 ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.xa, sm.full(stage),
@@ -219,7 +279,9 @@ __device__ void run_producer(const Smem& sm, const OperandMaps& maps, const Gram
 }
 
 // ------------------------------------------------------------------ MMA issuer
-__device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base) {
+template <bool kPair>
+__device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tmem_base) {
+    constexpr int kStages = Plan<kPair>::stages;
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
@@ -242,8 +304,9 @@ __device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base)
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
         const uint32_t idesc =
-            L.direct ? ptx::idesc_e4m3_f32_mnmajor(kTcBM, static_cast<uint32_t>(job.bn))
-                     : ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(job.bn));
+            kPair ? ptx::idesc_e4m3_f32(2 * kTcBM, static_cast<uint32_t>(job.bn))
+            : L.direct ? ptx::idesc_e4m3_f32_mnmajor(kTcBM, static_cast<uint32_t>(job.bn))
+                       : ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(job.bn));
         const int k_blocks = job.k_blocks;
         if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, L.timeout_ns,
                                     sm.abort_flag())) {
@@ -259,7 +322,16 @@ __device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base)
                 break;
             }
             ptx::tc_fence_after();
-            if (L.direct) {
+            if constexpr (kPair) {
+                const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
+                const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
+#pragma unroll
+                for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                    const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+                    ptx::mma_f8f6f4_pair(d_tmem, adesc + off, bdesc + off, idesc,
+                                         (kb | kk) != 0 ? 1u : 0u);
+                }
+            } else if (L.direct) {
                 // MN-major: 128-sample K-rows of 128 bytes, 128-variable atoms of
                 // B 16 KB apart; K step kk starts kk * 32 rows (4 atoms) further
                 const uint64_t adesc =
@@ -283,21 +355,30 @@ __device__ void run_mma(const Smem& sm, const GramLaunch& L, uint32_t tmem_base)
                                     (kb | kk) != 0 ? 1u : 0u);
                 }
             }
-            ptx::mma_commit(sm.empty(stage));   // frees the slot when these MMAs finish
+            if constexpr (kPair)
+                ptx::mma_commit_pair(sm.empty(stage));
+            else
+                ptx::mma_commit(sm.empty(stage));   // frees the slot when these MMAs finish
             if (++stage == kStages) {
                 stage = 0;
                 phase ^= 1u;
             }
         }
         if (!ok) break;
-        ptx::mma_commit(sm.tfull(acc));         // accumulator ready for the epilogue
+        if constexpr (kPair)                    // both CTAs' halves are ready
+            ptx::mma_commit_pair_multicast(sm.tfull(acc), static_cast<uint16_t>(3u));
+        else
+            ptx::mma_commit(sm.tfull(acc));     // accumulator ready for the epilogue
         if (++acc == 2) {
             acc = 0;
             acc_phase ^= 1u;
         }
     }
     // Wait (bounded) for every MMA issued by this thread before TMEM is freed.
-    ptx::mma_commit(sm.drain());
+    if constexpr (kPair)
+        ptx::mma_commit_pair(sm.drain());
+    else
+        ptx::mma_commit(sm.drain());
     const uint64_t d2 = ptx::globaltimer_ns() + 100000000ull;
     while (!ptx::mbar_try_wait(sm.drain(), 0)) {
         if (ptx::globaltimer_ns() > d2) {
@@ -320,8 +401,8 @@ __device__ __forceinline__ void store_one(const GramJob& g, int64_t row, int64_t
     }
 }
 
-template <int kMode>
-__device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_base) {
+template <int kMode, bool kPair>
+__device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tmem_base) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int lane_base = (warp & 3) * 32;             // TMEM lanes this warp may access
@@ -352,7 +433,8 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
         const int col_base = half * cols;
         const int64_t n_a = job.n_a, n_b = job.n_b;
         const bool sym = job.symmetric != 0;
-        const int64_t ibase = static_cast<int64_t>(tile.I) * kTcBM + lane_base;
+        const int64_t ibase = static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m +
+                              static_cast<int64_t>(sm.rank) * kTcBM + lane_base;
         const int64_t i = ibase + lane;
         const int64_t jstart = static_cast<int64_t>(tile.J) * job.bn + col_base;
         const bool row_ok = i < n_a;
@@ -508,7 +590,17 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
             }
         }
         ptx::tc_fence_before();
-        ptx::mbar_arrive(sm.tempty(acc));
+        if constexpr (kPair) {   // one arrival per warp, on CTA 0's barrier
+            __syncwarp();
+            if (lane == 0) {
+                if (sm.rank == 0)
+                    ptx::mbar_arrive(sm.tempty(acc));
+                else
+                    ptx::mbar_arrive_cluster(ptx::mapa_shared(sm.tempty(acc), 0u));
+            }
+        } else {
+            ptx::mbar_arrive(sm.tempty(acc));
+        }
         if (++acc == 2) {
             acc = 0;
             acc_phase ^= 1u;
@@ -516,15 +608,18 @@ __device__ void run_epilogue(const Smem& sm, const GramLaunch& L, uint32_t tmem_
     }
 }
 
-template <int kMode>
+template <int kMode, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__ GramLaunch L) {
     extern __shared__ uint8_t smem_raw[];
-    Smem sm;
+    Smem<kPair> sm;
     sm.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                          ~static_cast<uintptr_t>(1023));
+    sm.rank = kPair ? ptx::cluster_ctarank() : 0u;
+    constexpr int kStages = Plan<kPair>::stages;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const bool lead = sm.rank == 0;   // the CTA that loads and issues the MMAs
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -533,17 +628,19 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(sm.tfull(b), 1);
-            ptx::mbar_init(sm.tempty(b), kEpiWarps * 32);
+            // pair: one arrival per epilogue warp of both CTAs, on CTA 0
+            ptx::mbar_init(sm.tempty(b), kPair ? 2 * kEpiWarps : kEpiWarps * 32);
         }
         ptx::mbar_init(sm.drain(), 1);
         for (int q = 0; q < kQ; ++q) {
             ptx::mbar_init(sm.qfull(q), 1);
-            ptx::mbar_init(sm.qempty(q), 1 + kEpiWarps);   // MMA thread + one lane per warp
+            // MMA thread (CTA 0 only) + one lane per epilogue warp
+            ptx::mbar_init(sm.qempty(q), (lead ? 1 : 0) + kEpiWarps);
         }
         *sm.abort_flag() = 0;
         ptx::fence_barrier_init();
     }
-    if (warp == 0 && lane == 0) {
+    if (warp == 0 && lane == 0 && lead) {
         if (L.direct) {
             ptx::tma_prefetch_desc(&maps.xa);
             ptx::tma_prefetch_desc(&maps.xb);
@@ -554,70 +651,133 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
         }
     }
     if (warp == 1) {
-        ptx::tmem_alloc(ptx::smem_u32(sm.tmem_holder()), kTmemCols);
-        ptx::tmem_relinquish();
+        if constexpr (kPair) {
+            ptx::tmem_alloc_pair(ptx::smem_u32(sm.tmem_holder()), kTmemCols);
+            ptx::tmem_relinquish_pair();
+        } else {
+            ptx::tmem_alloc(ptx::smem_u32(sm.tmem_holder()), kTmemCols);
+            ptx::tmem_relinquish();
+        }
     }
     ptx::tc_fence_before();
     __syncthreads();
+    // pair: the partner's barriers are initialised before anything reaches them
+    if constexpr (kPair) ptx::cluster_sync();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *sm.tmem_holder();
 
     if (warp == 0) {
-        if (lane == 0) run_producer(sm, maps, L);
+        if (lane == 0) {
+            if (lead)
+                run_producer<kPair>(sm, maps, L);
+            else if constexpr (kPair)
+                run_feeder(sm, L);
+        }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) run_mma(sm, L, tmem_base);
+        if (lane == 0 && lead) run_mma<kPair>(sm, L, tmem_base);
         __syncwarp();
     } else {
-        run_epilogue<kMode>(sm, L, tmem_base);
+        run_epilogue<kMode, kPair>(sm, L, tmem_base);
     }
 
     ptx::tc_fence_before();
     __syncthreads();
+    // pair: neither CTA leaves (or frees tensor memory) while the other may
+    // still signal its barriers or be written by its copies
+    if constexpr (kPair) ptx::cluster_sync();
     if (warp == 1) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem_base, kTmemCols);
+        if constexpr (kPair)
+            ptx::tmem_dealloc_pair(tmem_base, kTmemCols);
+        else
+            ptx::tmem_dealloc(tmem_base, kTmemCols);
     }
+}
+
+template <bool kPair>
+cudaError_t set_smem_attrs() {
+    const int bytes = static_cast<int>(Plan<kPair>::smem_bytes);
+    cudaError_t e;
+    e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI, kPair>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeCounts, kPair>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(gram_tc_kernel<kTcModeCountsAdd, kPair>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int kMode>
+cudaError_t launch_pair(const OperandMaps& maps, const GramLaunch& L, int grid,
+                        cudaStream_t s) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = Plan<true>::smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gram_tc_kernel<kMode, true>, maps, L);
 }
 
 }  // namespace
 
-size_t gram_tc_smem_bytes() { return kSmemBytes; }
+size_t gram_tc_smem_bytes() { return Plan<false>::smem_bytes; }
 
 cudaError_t gram_tc_prepare() {
-    cudaError_t e;
-    e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
+    cudaError_t e = set_smem_attrs<false>();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeCounts>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(gram_tc_kernel<kTcModeCountsAdd>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kSmemBytes));
+    return set_smem_attrs<true>();
 }
 
-int64_t gram_tile_count(int64_t n_a, int64_t n_b, int bn, bool symmetric) {
-    const int64_t TI = (n_a + kTcBM - 1) / kTcBM, TJ = (n_b + bn - 1) / bn;
+int gram_tc_pair_clusters() {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = Plan<true>::smem_bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, gram_tc_kernel<kTcModeMI, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int64_t gram_tile_count(int64_t n_a, int64_t n_b, int bn, bool symmetric, int bm) {
+    const int64_t TI = (n_a + bm - 1) / bm, TJ = (n_b + bn - 1) / bn;
     if (!symmetric) return TI * TJ;
     int64_t c = 0;
-    for (int64_t J = 0; J < TJ; ++J)   // row blocks I with 128 I <= bn J + bn - 1
-        c += std::min<int64_t>(TI, (J * bn + bn - 1) / kTcBM + 1);
+    for (int64_t J = 0; J < TJ; ++J)   // row blocks I with bm I <= bn J + bn - 1
+        c += std::min<int64_t>(TI, (J * bn + bn - 1) / bm + 1);
     return c;
 }
 
 void gram_tiles(int job, int64_t n_a, int64_t n_b, int bn, bool symmetric, int group_cols,
-                GramTile* out) {
-    const int64_t TI = (n_a + kTcBM - 1) / kTcBM, TJ = (n_b + bn - 1) / bn;
+                GramTile* out, int bm) {
+    const int64_t TI = (n_a + bm - 1) / bm, TJ = (n_b + bn - 1) / bn;
     const int64_t group = std::max(1, group_cols);
     int64_t k = 0;
     for (int64_t g0 = 0; g0 < TJ; g0 += group) {
         const int64_t g1 = std::min<int64_t>(TJ, g0 + group);
         for (int64_t I = 0; I < TI; ++I)
             for (int64_t J = g0; J < g1; ++J) {
-                if (symmetric && I * kTcBM > J * bn + bn - 1) continue;   // below the diagonal
+                if (symmetric && I * bm > J * bn + bn - 1) continue;   // below the diagonal
                 out[k++] = GramTile{job, static_cast<int32_t>(I), static_cast<int32_t>(J), 0};
             }
     }
@@ -626,15 +786,25 @@ void gram_tiles(int job, int64_t n_a, int64_t n_b, int bn, bool symmetric, int g
 cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int grid,
                            cudaStream_t s) {
     if (L.num_tiles <= 0 || grid <= 0) return cudaSuccess;
+    if (L.pair) {
+        if (grid % 2 != 0 || L.direct) return cudaErrorInvalidValue;
+        switch (L.mode) {
+            case kTcModeMI: return launch_pair<kTcModeMI>(maps, L, grid, s);
+            case kTcModeCounts: return launch_pair<kTcModeCounts>(maps, L, grid, s);
+            case kTcModeCountsAdd: return launch_pair<kTcModeCountsAdd>(maps, L, grid, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    constexpr size_t kSmem = Plan<false>::smem_bytes;
     switch (L.mode) {
         case kTcModeMI:
-            gram_tc_kernel<kTcModeMI><<<grid, kThreads, kSmemBytes, s>>>(maps, L);
+            gram_tc_kernel<kTcModeMI, false><<<grid, kThreads, kSmem, s>>>(maps, L);
             break;
         case kTcModeCounts:
-            gram_tc_kernel<kTcModeCounts><<<grid, kThreads, kSmemBytes, s>>>(maps, L);
+            gram_tc_kernel<kTcModeCounts, false><<<grid, kThreads, kSmem, s>>>(maps, L);
             break;
         case kTcModeCountsAdd:
-            gram_tc_kernel<kTcModeCountsAdd><<<grid, kThreads, kSmemBytes, s>>>(maps, L);
+            gram_tc_kernel<kTcModeCountsAdd, false><<<grid, kThreads, kSmem, s>>>(maps, L);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -147,6 +147,10 @@ struct GramLaunch {
     // subnormal 2^-9, so the accumulator holds count * 2^-18 (exact below 2^24
     // samples) and the epilogue scales it back by 2^18.
     int direct;
+    // 1: CTA-pair launch (clusters of 2, tcgen05 cta_group::2): tiles of 256 x
+    // 256 (GramTile.I counts 256-row blocks; every job has bn = 256), packed
+    // operands only, static tile order; the grid is an even number of CTAs.
+    int pair;
     // Dynamic tile order: CTAs take the next tile from this counter (zero at
     // launch), so the tiles in flight are always a contiguous window of the
     // list.  Null: static round-robin (tile blockIdx.x + k * gridDim.x).
@@ -166,14 +170,17 @@ bool make_operand_maps(OperandMaps* maps, const uint8_t* P, int64_t total_rows);
 // Needs n1, n2 multiples of 16 and 16-byte aligned X, Y.
 bool make_direct_maps(OperandMaps* maps, const uint8_t* X, int64_t m, int64_t n1,
                       const uint8_t* Y, int64_t n2);
-// Tiles of one job in the kernel's order (groups of group_cols column blocks).
-int64_t gram_tile_count(int64_t n_a, int64_t n_b, int bn, bool symmetric);
+// Tiles of one job in the kernel's order (groups of group_cols column blocks),
+// bm rows (128; 256 for a CTA-pair launch) by bn columns.
+int64_t gram_tile_count(int64_t n_a, int64_t n_b, int bn, bool symmetric, int bm = kTcBM);
 void gram_tiles(int job, int64_t n_a, int64_t n_b, int bn, bool symmetric, int group_cols,
-                GramTile* out);
+                GramTile* out, int bm = kTcBM);
 cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int grid,
                            cudaStream_t s);
 size_t gram_tc_smem_bytes();
-cudaError_t gram_tc_prepare();   // set the kernel's shared-memory attribute (current device)
+cudaError_t gram_tc_prepare();   // set the kernels' shared-memory attribute (current device)
+// CTA pairs (clusters of 2) of the pair kernel that fit on the device at once.
+int gram_tc_pair_clusters();
 
 // Set the text gbmi_last_error_string() returns on this host thread.
 void set_last_error(const char* msg);

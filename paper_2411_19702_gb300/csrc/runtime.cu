@@ -130,6 +130,7 @@ gbmi_status get_ctx(DeviceCtx** out) {
         GBMI_CUDA(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev),
                   "cudaDeviceGetAttribute");
         GBMI_CUDA(gram_tc_prepare(), "cudaFuncSetAttribute");
+        c.pair_clusters = gram_tc_pair_clusters();
         GBMI_TRY(ensure(c.err, 256, "error word"));
         GBMI_CUDA(cudaMemset(c.err.p, 0, 256), "cudaMemset");
         c.ready = true;

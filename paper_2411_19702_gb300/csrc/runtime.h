@@ -30,6 +30,7 @@ struct Options {
     int max_ctas = 0;
     int tile_n = 0;                      // 0: tuner table / cost model; else forced 64/128/256
     int direct = 0;                      // 1: no pack where X's rows are 16-byte multiples
+    int pair = 1;                        // 1: CTA-pair (cta_group::2) Gram where it fills the GPU
 };
 
 struct DeviceCtx {
@@ -40,7 +41,8 @@ struct DeviceCtx {
     int64_t T_len = 0;
     // tile-list cache of the single-dataset path
     int64_t tl_na = -1, tl_nb = -1;
-    int tl_sym = -1, tl_group = -1, tl_bn = -1;
+    int tl_sym = -1, tl_group = -1, tl_bn = -1, tl_bm = -1;
+    int pair_clusters = 0;   // CTA pairs of the pair Gram kernel resident at once
     std::vector<GramTile> tl_host;
 };
 

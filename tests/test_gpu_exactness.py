@@ -78,13 +78,15 @@ def test_random_counts_at_precision_m_match_popcount():
     assert torch.equal(torch.diagonal(a), X.sum(dim=0, dtype=torch.int32))
 
 
-def test_bounded_wait_times_out_and_context_survives():
+@pytest.mark.parametrize("pair", [0, 2], ids=["single", "pair"])
+def test_bounded_wait_times_out_and_context_survives(pair):
     """The fused kernel's loader issues no copies (test hook), so its MMA
     thread's wait on the first stage can never complete: it must give up after
     the timeout, report GBMI_ERR_TIMEOUT, free its tensor memory and leave the
-    context usable."""
+    context usable (single-CTA and CTA-pair kernels)."""
     X = torch.from_numpy((np.random.default_rng(1).random((512, 300)) < 0.3)
                          .astype(np.uint8)).cuda()
+    gbmi.set_option(gbmi.OPT_PAIR, pair)
     gbmi.set_option(gbmi.OPT_TIMEOUT_NS, 50_000_000)
     gbmi.set_option(gbmi.OPT_DEBUG_FLAGS, 1)
     gbmi.mi_all_pairs(X, path="fused")
@@ -95,5 +97,6 @@ def test_bounded_wait_times_out_and_context_survives():
     gbmi.set_option(gbmi.OPT_TIMEOUT_NS, 2_000_000_000)
     out = gbmi.mi_all_pairs(X, path="fused")
     gbmi.sync()
+    gbmi.set_option(gbmi.OPT_PAIR, 1)
     want, _ = oracle.mi_matrix(X.cpu().numpy())
     assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - want)) <= 1e-6
