@@ -9,9 +9,11 @@
 //
 // A CTA owns 128 variables and a run of 128-sample tiles.  Each tile is read
 // with coalesced 16-byte loads (the next tile's loads are in flight while the
-// current one is transposed), transposed in shared memory in 4x4 byte blocks
-// with byte permutes and written out with 16-byte stores.  A grouped launch
-// covers many datasets: CTA c works for the job whose CTA range holds c.
+// current one is transposed), transposed through shared memory in 4x4 byte
+// blocks with byte permutes, and written out so that every warp store covers
+// whole 128-byte rows of P (a tile's output is one contiguous 16 KB block).
+// A grouped launch covers many datasets: CTA c works for the job whose CTA
+// range holds c.
 #include "internal.cuh"
 
 namespace gbmi {
@@ -84,11 +86,21 @@ __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
     return ((x * 0x01020408u) >> 24) & 0xFu;
 }
 
+// Thread layout of the transpose: warp w owns variables 16 w .. 16 w + 15 of
+// the CTA's 128 and all 128 samples of the tile; lane = 4 sg + vg takes the
+// 4 variables 16 w + 4 vg .. + 3 and the 16 samples 16 sg .. + 15.  A store
+// instruction of the warp then writes 4 whole 128-byte rows of P.  The tile
+// sits in shared memory with its 16-byte chunks XOR-swizzled by the row's
+// 16-row group (chunk ^ (r / 16) % 8), which keeps both the row-wise fill
+// and the column-wise reads of the transpose free of bank conflicts.
 __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, const int64_t by,
-                                         uint8_t* S, int (*red)[kTileJ]) {
+                                         uint8_t* S) {
     const int t = threadIdx.x;
-    const int w = t >> 5;          // warp: 16-sample slice of the tile
-    const int jq = t & 31;         // lane: group of 4 variables
+    const int w = t >> 5;
+    const int lane = t & 31;
+    const int vg = lane & 3;
+    const int sg = lane >> 2;
+    const int colw = 4 * w + vg;   // word column (4 variables) of this thread
     const int64_t j0 = bx * kTileJ;
     const int64_t tiles_total = a.ldp / kTileR;
     const int64_t tile_begin = by * a.tpc;
@@ -96,7 +108,7 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
     const bool vec = a.vec != 0;
 
     int colsum[4] = {0, 0, 0, 0};
-    uint32_t* S32 = reinterpret_cast<uint32_t*>(S);
+    const uint32_t* S32 = reinterpret_cast<const uint32_t*>(S);
 
     // the next tile's 16-byte loads are issued before the current tile is
     // transposed and stored, so they overlap that work
@@ -122,22 +134,26 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
 
     for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
         const int64_t r0 = tile * kTileR;
-        // ---- 128 samples x 128 variables into S[r][j]
+        // ---- 128 samples x 128 variables into S (row r, swizzled 16-byte chunks)
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(S + (q * 32 + (t >> 3)) * kTileJ + (t & 7) * 16) = pre[q];
+        for (int q = 0; q < 4; ++q) {
+            const int r = q * 32 + (t >> 3);
+            const int chunk = (t & 7) ^ ((r >> 4) & 7);
+            *reinterpret_cast<uint4*>(S + r * kTileJ + chunk * 16) = pre[q];
+        }
         __syncthreads();
         if (tile + 1 < tile_end) load_tile(tile + 1);
 
-        // ---- transpose: this thread owns samples r0 + 16 w .. +15 of variables 4 jq .. +3
-        uint32_t col[4][4];   // col[c][g]: variable 4 jq + c, samples 4 g .. 4 g + 3
+        // ---- transpose: variables 16 w + 4 vg .. +3, samples 16 sg .. +15
+        const int swz = colw ^ (4 * sg);   // rows 16 sg .. +15 share one swizzle
+        uint32_t col[4][4];   // col[c][g]: variable 16 w + 4 vg + c, samples 16 sg + 4 g .. +3
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            const int rr = w * 16 + g * 4;
-            const uint32_t w0 = nz_bytes(S32[(rr + 0) * (kTileJ / 4) + jq]);
-            const uint32_t w1 = nz_bytes(S32[(rr + 1) * (kTileJ / 4) + jq]);
-            const uint32_t w2 = nz_bytes(S32[(rr + 2) * (kTileJ / 4) + jq]);
-            const uint32_t w3 = nz_bytes(S32[(rr + 3) * (kTileJ / 4) + jq]);
+            const int rr = sg * 16 + g * 4;
+            const uint32_t w0 = nz_bytes(S32[(rr + 0) * (kTileJ / 4) + swz]);
+            const uint32_t w1 = nz_bytes(S32[(rr + 1) * (kTileJ / 4) + swz]);
+            const uint32_t w2 = nz_bytes(S32[(rr + 2) * (kTileJ / 4) + swz]);
+            const uint32_t w3 = nz_bytes(S32[(rr + 3) * (kTileJ / 4) + swz]);
             // column sums: bytes of w0+w1+w2+w3 are per-variable counts (<= 4)
             const uint32_t s4 = w0 + w1 + w2 + w3;
             colsum[0] += s4 & 0xFF;
@@ -148,10 +164,10 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
         }
         __syncthreads();   // S is rewritten by the next tile
 
-        const int64_t rbase = r0 + w * 16;
+        const int64_t rbase = r0 + sg * 16;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const int64_t j = j0 + jq * 4 + c;
+            const int64_t j = j0 + colw * 4 + c;
             if (j >= a.rows_p) continue;
             if (a.P != nullptr) {
                 uint4 o;
@@ -159,7 +175,7 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
                 o.y = col[c][1] * 0x38u;
                 o.z = col[c][2] * 0x38u;
                 o.w = col[c][3] * 0x38u;
-                *reinterpret_cast<uint4*>(a.P + (tile * a.rows_p + j) * kTileR + w * 16) = o;
+                *reinterpret_cast<uint4*>(a.P + (tile * a.rows_p + j) * kTileR + sg * 16) = o;
             }
             if (a.Bp != nullptr) {
                 const uint32_t bits = bytes_to_nibble(col[c][0]) |
@@ -173,30 +189,28 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
     }
 
     if (a.v == nullptr) return;
+    // sum over the 8 sample groups of the warp (lane bits 2-4), one add per variable
 #pragma unroll
-    for (int c = 0; c < 4; ++c) red[w][jq * 4 + c] = colsum[c];
-    __syncthreads();
-    if (t < kTileJ) {
-        int s = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) s += red[k][t];
-        const int64_t j = j0 + t;
-        if (j < a.n && s != 0) atomicAdd(a.v + j, s);
+    for (int c = 0; c < 4; ++c) {
+        int x = colsum[c];
+        x += __shfl_xor_sync(0xffffffffu, x, 4);
+        x += __shfl_xor_sync(0xffffffffu, x, 8);
+        x += __shfl_xor_sync(0xffffffffu, x, 16);
+        const int64_t j = j0 + colw * 4 + c;
+        if (sg == 0 && j < a.n && x != 0) atomicAdd(a.v + j, x);
     }
 }
 
 __global__ void __launch_bounds__(kPackThreads, 4)   // 4 CTAs per SM: loads in flight
 pack_kernel(const PackJob job) {
     __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
-    __shared__ int red[8][kTileJ];
     const int64_t c = blockIdx.x;
-    pack_cta(job, c % job.gx, c / job.gx, S, red);
+    pack_cta(job, c % job.gx, c / job.gx, S);
 }
 
 __global__ void __launch_bounds__(kPackThreads, 4)
 pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs) {
     __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
-    __shared__ int red[8][kTileJ];
     const int64_t c = blockIdx.x;
     int lo = 0, hi = njobs - 1;   // last job whose cta_begin <= c
     while (lo < hi) {
@@ -205,7 +219,7 @@ pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs) {
     }
     const PackJob job = jobs[lo];
     const int64_t cl = c - job.cta_begin;
-    pack_cta(job, cl % job.gx, cl / job.gx, S, red);
+    pack_cta(job, cl % job.gx, cl / job.gx, S);
 }
 
 __global__ void validate_kernel(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
