@@ -388,6 +388,49 @@ def measure_out_of_core(dev, m=100_000, n=50_000, reps=2, seed=6):
     return res
 
 
+# --------------------------------------------------------------- sparse input
+def measure_sparse(dev, m=100_000, n=10_000, densities=(0.01, 0.005, 0.001), reps=3, seed=7):
+    """Paper-shape inputs at 99%, 99.5% and 99.9% zeros (iid Bernoulli): the CSR path
+    (inputs resident in CSR) against the dense fused path on the same matrix."""
+    import torch
+
+    from paper_2411_19702_gb300 import gbmi
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    res = []
+    for d in densities:
+        X = (torch.rand((m, n), generator=g, device=dev) < d).to(torch.uint8)
+        rp, ci = gbmi.csr_from_dense(X)
+        torch.cuda.synchronize(dev)
+
+        def timed(fn):
+            fn()
+            gbmi.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            gbmi.sync()
+            return e0.elapsed_time(e1) / reps
+        sparse_ms = timed(lambda: gbmi.mi_all_pairs_csr(rp, ci, n, out=out))
+        sparse_out = out.clone()
+        dense_ms = timed(lambda: gbmi.mi_all_pairs(X, out=out, path="fused"))
+        rows = torch.arange(0, n, 211, device=dev)
+        diff = float((sparse_out[rows] - out[rows]).abs().max())
+        res.append({"zeros_pct": 100.0 * (1.0 - d), "nnz": int(ci.numel()),
+                    "pair_increments": int(((rp[1:] - rp[:-1]) * (rp[1:] - rp[:-1] + 1) // 2)
+                                           .sum()),
+                    "csr_ms": sparse_ms, "dense_fused_ms": dense_ms,
+                    "csr_over_dense_speedup": dense_ms / sparse_ms,
+                    "max_abs_diff_sampled_rows": diff})
+        del X, rp, ci, sparse_out
+        torch.cuda.empty_cache()
+    return {"m": m, "n": n, "densities": res}
+
+
 # --------------------------------------------------------------- serving
 def serve_pool(k_all=48, k_cross=24, seed=5):
     """Dataset shapes of the serving workload's pool: all-pairs (m, n) and cross (m, n1, n2)."""
@@ -689,6 +732,9 @@ def run_ours(args):
     batch = None
     if not args.skip_batch:
         batch = measure_batch(dev)
+    sparse = None
+    if not args.skip_sparse and rank == 0:
+        sparse = measure_sparse(dev)
     out_of_core = None
     if not args.skip_ooc and rank == 0:
         out_of_core = measure_out_of_core(dev)
@@ -738,6 +784,7 @@ def run_ours(args):
         "batch": batch,
         "serving": serving,
         "out_of_core": out_of_core,
+        "sparse": sparse,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
@@ -762,6 +809,7 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-ooc", action="store_true")
+    ap.add_argument("--skip-sparse", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:

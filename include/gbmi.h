@@ -159,6 +159,27 @@ gbmi_status gbmi_mi_all_pairs_to_host(const uint8_t* X, int64_t m, int64_t n, fl
 gbmi_status gbmi_mi_cross_to_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
                                   int64_t n2, float* host_out, int64_t panel_rows);
 
+/* ------------------------------------------------------------ sparse input */
+
+/* Sparse input (the paper's sparse-matrix variant, Opt-SS, Sec. 4.2.3): X
+ * given by samples in CSR form, device pointers: row_ptr[m + 1] (int64, row r
+ * holds col_idx[row_ptr[r] .. row_ptr[r + 1])), col_idx[nnz] (int32) = the
+ * variables that are 1 in that sample, strictly increasing.  A sample with k
+ * ones adds 1 to N11[a][b] for each of its k (k + 1) / 2 pairs a <= b (atomic
+ * adds; the diagonal gives the column counts), so the work follows
+ * sum_r k_r^2 / 2 instead of m * n^2 / 2: it beats the dense tensor-core path
+ * only for very sparse data.  gbmi_mi_all_pairs_csr writes the n x n FP32 MI
+ * matrix (out, as mi_all_pairs; values identical to the dense paths);
+ * gbmi_counts_all_pairs_csr writes the symmetric n x n int32 counts.  A
+ * malformed row (bounds outside [0, nnz], an index outside [0, n), indices not
+ * strictly increasing) is skipped and reported as GBMI_ERR_ARG by gbmi_sync.
+ * The library keeps an n x n int32 count matrix in its workspace for the MI
+ * call.  Asynchronous on the library's stream. */
+gbmi_status gbmi_mi_all_pairs_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t m,
+                                  int64_t n, int64_t nnz, float* out);
+gbmi_status gbmi_counts_all_pairs_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t m,
+                                      int64_t n, int64_t nnz, int32_t* n11);
+
 /* ------------------------------------------------------ counts and pieces */
 
 /* Co-occurrence counts N11 = X^T X (G11 of Sec. 2 step 2) as int32, n x n,

@@ -27,6 +27,10 @@ constexpr double kTinyWork = 6.0e7;
 
 // Status for a non-zero device error word.
 gbmi_status error_word_status(unsigned int err) {
+    if (err & kErrBadCsr)
+        return fail(GBMI_ERR_ARG,
+                    "malformed CSR input: a row outside [0, nnz], an index outside [0, n) or "
+                    "indices not strictly increasing (those rows were skipped)");
     if (err & kErrBadOperand)
         return fail(GBMI_ERR_ARG, "a direct operand copy was not 16-byte aligned (skipped)");
     if ((err & ~static_cast<unsigned int>(kErrNotBinary)) != 0)
@@ -313,8 +317,12 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
         GBMI_TRY(run_gram(c, L.total_rows,
                           tc_job(L, m, n1, n2, sym, bn, va, vb, mp, nullptr, N11), m,
                           kTcModeCounts, L.direct ? &L.maps : nullptr));
-        GBMI_LAUNCH(launch_mi_from_counts(N11, n2, va, vb, n1, n2, mp, out, n2, g_stream),
-                    "mi_from_counts");
+        if (sym)
+            GBMI_LAUNCH(launch_mi_from_counts_sym(N11, n2, va, n1, mp, out, n2, g_stream),
+                        "mi_from_counts");
+        else
+            GBMI_LAUNCH(launch_mi_from_counts(N11, n2, va, vb, n1, n2, mp, out, n2, g_stream),
+                        "mi_from_counts");
         return GBMI_OK;
     }
     // popcount: Gram and MI epilogue in one kernel
@@ -606,6 +614,43 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
     return st;
 }
 
+// Sparse input (CSR by samples): pair counts into the upper triangle of N11,
+// then either the symmetric count matrix or the MI of every pair.
+gbmi_status csr_impl(const int64_t* row_ptr, const int32_t* col, int64_t m, int64_t n,
+                     int64_t nnz, float* out, int32_t* n11) {
+    if (row_ptr == nullptr || (col == nullptr && nnz > 0) || (out == nullptr && n11 == nullptr))
+        return fail(GBMI_ERR_ARG, "null pointer");
+    GBMI_TRY(check_sizes(m, n, n));
+    if (nnz < 0) return fail(GBMI_ERR_ARG, "nnz must be >= 0");
+    if (nnz > m * n) return fail(GBMI_ERR_ARG, "nnz exceeds m * n");
+    DeviceCtx* cp = nullptr;
+    GBMI_TRY(rt::get_ctx(&cp));
+    DeviceCtx& c = *cp;
+    const size_t cbytes = static_cast<size_t>(n) * n * 4;
+    int32_t* N11 = n11;
+    if (N11 == nullptr) {
+        GBMI_TRY(ensure(c.counts, cbytes, "count matrix"));
+        N11 = static_cast<int32_t*>(c.counts.p);
+    }
+    GBMI_CUDA(cudaMemsetAsync(N11, 0, cbytes, g_stream), "zero counts");
+    GBMI_LAUNCH(launch_csr_pair_counts(row_ptr, col, m, n, nnz, N11,
+                                       static_cast<unsigned int*>(c.err.p), c.sm_count, g_stream),
+                "csr_pair_counts");
+    if (n11 != nullptr) {
+        GBMI_LAUNCH(launch_mirror_upper(N11, n, g_stream), "mirror_upper");
+        return GBMI_OK;
+    }
+    GBMI_TRY(ensure(c.va, static_cast<size_t>(n) * 4, "column counts"));
+    GBMI_LAUNCH(launch_diag(N11, n, static_cast<int32_t*>(c.va.p), g_stream), "diag");
+    MiParams mp;
+    GBMI_TRY(rt::mi_params(c, m, &mp));
+    const MiVar* vars = nullptr;
+    GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.va.p), n, mp, c.ha, &vars));
+    GBMI_LAUNCH(launch_mi_from_counts_sym(N11, n, vars, n, mp, out, n, g_stream, 1),
+                "mi_from_counts");
+    return GBMI_OK;
+}
+
 }  // namespace
 }  // namespace gbmi
 
@@ -658,6 +703,18 @@ gbmi_status gbmi_mi_cross_to_host(const uint8_t* X, const uint8_t* Y, int64_t m,
                                   int64_t n2, float* host_out, int64_t panel_rows) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     return blocked_impl(X, Y, m, n1, n2, host_out, panel_rows, false);
+}
+
+gbmi_status gbmi_mi_all_pairs_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t m,
+                                  int64_t n, int64_t nnz, float* out) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    return csr_impl(row_ptr, col_idx, m, n, nnz, out, nullptr);
+}
+
+gbmi_status gbmi_counts_all_pairs_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t m,
+                                      int64_t n, int64_t nnz, int32_t* n11) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    return csr_impl(row_ptr, col_idx, m, n, nnz, nullptr, n11);
 }
 
 gbmi_status gbmi_counts_all_pairs(const uint8_t* X, int64_t m, int64_t n, int32_t* n11,

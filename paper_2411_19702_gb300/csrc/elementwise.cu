@@ -58,7 +58,70 @@ __global__ void mi_from_counts_kernel(const int32_t* N11, int64_t ld_n11, const 
     }
 }
 
+// Symmetric counts (all pairs of one matrix): only tiles with I <= J of 32 x 32
+// pairs are evaluated; each value is written to (i, j) directly and to (j, i)
+// through a shared-memory transpose, so both writes are coalesced rows.  A
+// diagonal tile evaluates its 32 x 32 pairs itself.
+constexpr int kSymTile = 32;
+
+__global__ void __launch_bounds__(256)
+mi_from_counts_sym_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* vars, int64_t n,
+                          const MiParams P, float* out, int64_t ld_out, int64_t tiles_per_side,
+                          int upper_only) {
+    __shared__ float T[kSymTile][kSymTile + 1];
+    // tile index -> (I, J) with I <= J, row-major over the upper triangle
+    // first tile of row I: S(I) = I * tps - I (I - 1) / 2; take the largest I
+    // with S(I) <= t (closed form, then exact integer correction)
+    const int64_t t = blockIdx.x, tps = tiles_per_side;
+    const double b = 2.0 * static_cast<double>(tps) + 1.0;
+    int64_t I = static_cast<int64_t>((b - sqrt(b * b - 8.0 * static_cast<double>(t))) * 0.5);
+    auto first = [tps](int64_t r) { return r * tps - r * (r - 1) / 2; };
+    while (I > 0 && first(I) > t) --I;
+    while (I + 1 < tps && first(I + 1) <= t) ++I;
+    const int64_t J = I + (t - first(I));
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    const int64_t j = J * kSymTile + tx;
+    MiVar B;
+    const bool jok = j < n;
+    if (jok) B = load_var(vars + j);
+#pragma unroll
+    for (int k = 0; k < kSymTile / 8; ++k) {
+        const int r = ty + 8 * k;
+        const int64_t i = I * kSymTile + r;
+        float v = 0.f;
+        if (jok && i < n) {
+            const MiVar A = load_var(vars + i);
+            // upper_only: only N11[a][b], a <= b, is filled
+            const int64_t lo = (upper_only && i > j) ? j : i, hi = (upper_only && i > j) ? i : j;
+            v = mi_pair(N11[lo * ld_n11 + hi], A, B, P);
+            out[i * ld_out + j] = v;
+        }
+        T[r][tx] = v;
+    }
+    if (I == J) return;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSymTile / 8; ++k) {
+        const int c = ty + 8 * k;                 // column of the tile -> row of the mirror
+        const int64_t jj = J * kSymTile + c;
+        const int64_t ii = I * kSymTile + tx;
+        if (jj < n && ii < n) out[jj * ld_out + ii] = T[tx][c];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mi_from_counts_sym(const int32_t* N11, int64_t ld_n11, const MiVar* vars,
+                                      int64_t n, const MiParams& P, float* out, int64_t ld_out,
+                                      cudaStream_t s, int upper_only) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t tps = (n + kSymTile - 1) / kSymTile;
+    const int64_t tiles = tps * (tps + 1) / 2;
+    if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    mi_from_counts_sym_kernel<<<static_cast<unsigned>(tiles), 256, 0, s>>>(
+        N11, ld_n11, vars, n, P, out, ld_out, tps, upper_only);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_zero_u32(void* p, int64_t words, cudaStream_t s) {
     const int64_t blocks = (words + 255) / 256;

@@ -39,6 +39,7 @@ enum : uint32_t {
     kErrTimeoutDrain = 8u,
     kErrNotBinary = 16u,     // the direct operand path met a byte other than 0 / 1
     kErrBadOperand = 32u,    // a direct operand tile did not start on a 16-byte boundary
+    kErrBadCsr = 64u,        // a CSR row was out of bounds, out of range or not increasing
 };
 
 // -------------------------------------------------------------- pack kernel
@@ -81,6 +82,20 @@ cudaError_t launch_mi_vars_grouped(const int32_t* v, const int64_t* var_begin, i
 cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const MiVar* va,
                                   const MiVar* vb, int64_t n1, int64_t n2, const MiParams& P,
                                   float* out, int64_t ld_out, cudaStream_t s);
+// All pairs of one matrix (N11 symmetric): each unordered pair evaluated once,
+// written to (i, j) and (j, i).  upper_only: only N11[a][b], a <= b, is read.
+cudaError_t launch_mi_from_counts_sym(const int32_t* N11, int64_t ld_n11, const MiVar* vars,
+                                      int64_t n, const MiParams& P, float* out, int64_t ld_out,
+                                      cudaStream_t s, int upper_only = 0);
+
+// ------------------------------------------------------------ sparse input
+// Upper triangle (with the diagonal) of N11 from X in CSR by samples (N11
+// zeroed before); a malformed row sets kErrBadCsr and is skipped.
+cudaError_t launch_csr_pair_counts(const int64_t* row_ptr, const int32_t* col, int64_t m,
+                                   int64_t n, int64_t nnz, int32_t* N11, unsigned int* err,
+                                   int sm_count, cudaStream_t s);
+cudaError_t launch_diag(const int32_t* N11, int64_t n, int32_t* v, cudaStream_t s);
+cudaError_t launch_mirror_upper(int32_t* N11, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------- popcount Gram
 struct PopcArgs {

@@ -85,6 +85,8 @@ def load(path: str | None = None):
             "gbmi_mi_batch": [vp, i32],
             "gbmi_mi_all_pairs_to_host": [vp, i64, i64, vp, i64],
             "gbmi_mi_cross_to_host": [vp, vp, i64, i64, i64, vp, i64],
+            "gbmi_mi_all_pairs_csr": [vp, vp, i64, i64, i64, vp],
+            "gbmi_counts_all_pairs_csr": [vp, vp, i64, i64, i64, vp],
             "gbmi_server_create": [i64, i32, vp],
             "gbmi_server_add_dataset": [vp, vp, i64, i64, vp],
             "gbmi_server_remove_dataset": [vp, i64],
@@ -334,6 +336,55 @@ def mi_cross_to_host(X, Y, out=None, panel_rows=0):
         _check(lib.gbmi_mi_cross_to_host(X.data_ptr(), Y.data_ptr(), m, n1, n2, out.data_ptr(),
                                          int(panel_rows)))
     return out
+
+
+def _csr(row_ptr, col_idx, n):
+    import torch
+    if not (isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda and row_ptr.dtype == torch.int64
+            and row_ptr.dim() == 1 and row_ptr.numel() >= 2):
+        raise TypeError("row_ptr must be a 1-D int64 CUDA tensor of m + 1 entries")
+    if not (isinstance(col_idx, torch.Tensor) and col_idx.is_cuda and col_idx.dtype == torch.int32
+            and col_idx.dim() == 1):
+        raise TypeError("col_idx must be a 1-D int32 CUDA tensor")
+    return row_ptr.contiguous(), col_idx.contiguous(), row_ptr.numel() - 1, int(n)
+
+
+def mi_all_pairs_csr(row_ptr, col_idx, n, out=None):
+    """n x n MI matrix of X given in CSR by samples (int64 row_ptr, int32 col_idx)."""
+    import torch
+    row_ptr, col_idx, m, n = _csr(row_ptr, col_idx, n)
+    with torch.cuda.device(row_ptr.device):
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float32, device=row_ptr.device)
+        lib = _bind_stream(row_ptr.device)
+        _check(lib.gbmi_mi_all_pairs_csr(row_ptr.data_ptr(), col_idx.data_ptr() if col_idx.numel()
+                                         else None, m, n, col_idx.numel(), out.data_ptr()))
+    return out
+
+
+def counts_all_pairs_csr(row_ptr, col_idx, n, out=None):
+    """n x n int32 co-occurrence counts of X given in CSR by samples."""
+    import torch
+    row_ptr, col_idx, m, n = _csr(row_ptr, col_idx, n)
+    with torch.cuda.device(row_ptr.device):
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.int32, device=row_ptr.device)
+        lib = _bind_stream(row_ptr.device)
+        _check(lib.gbmi_counts_all_pairs_csr(row_ptr.data_ptr(), col_idx.data_ptr()
+                                             if col_idx.numel() else None, m, n, col_idx.numel(),
+                                             out.data_ptr()))
+    return out
+
+
+def csr_from_dense(X):
+    """CSR by samples of a device uint8 0/1 matrix (torch ops; input preparation)."""
+    import torch
+    X = _prep(X)
+    nz = torch.nonzero(X)                       # row-major order: rows, then increasing columns
+    counts = torch.bincount(nz[:, 0], minlength=X.shape[0])
+    row_ptr = torch.zeros(X.shape[0] + 1, dtype=torch.int64, device=X.device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    return row_ptr, nz[:, 1].to(torch.int32).contiguous()
 
 
 class _Job(ctypes.Structure):

@@ -94,3 +94,13 @@ def test_out_of_core_argument_errors_need_no_gpu():
     assert b"panel_rows" in lib.gbmi_last_error_string()
     assert lib.gbmi_mi_all_pairs_to_host(16, (1 << 24) + 1, 4, 16, 0) == gbmi.ERR_ARG
     assert lib.gbmi_mi_cross_to_host(16, None, 10, 4, 4, 16, 0) == gbmi.ERR_ARG
+
+
+def test_csr_argument_errors_need_no_gpu():
+    lib = gbmi.load()
+    assert lib.gbmi_mi_all_pairs_csr(None, 16, 10, 4, 3, 16) == gbmi.ERR_ARG
+    assert lib.gbmi_mi_all_pairs_csr(16, None, 10, 4, 3, 16) == gbmi.ERR_ARG   # nnz > 0, no col
+    assert lib.gbmi_mi_all_pairs_csr(16, 16, 10, 4, -1, 16) == gbmi.ERR_ARG
+    assert lib.gbmi_mi_all_pairs_csr(16, 16, 10, 4, 41, 16) == gbmi.ERR_ARG   # nnz > m * n
+    assert lib.gbmi_counts_all_pairs_csr(16, 16, 0, 4, 0, 16) == gbmi.ERR_ARG  # m = 0
+    assert lib.gbmi_counts_all_pairs_csr(16, 16, 10, 4, 3, None) == gbmi.ERR_ARG
