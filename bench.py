@@ -318,6 +318,10 @@ def measure_batch(dev, reps=3, k=512, seed=4):
 
     plan = gbmi.Batch(Xs)
     batch_ms = timed(plan.run, reps)
+    l0 = gbmi.launch_count()
+    plan.run()
+    gbmi.sync()
+    launches_per_run = gbmi.launch_count() - l0
     outs = plan.outs
     sep_out = [torch.empty_like(o) for o in outs]
 
@@ -337,7 +341,7 @@ def measure_batch(dev, reps=3, k=512, seed=4):
            "separate_plain_ms": plain_ms, "separate_fused_ms": fused_ms,
            "speedup_vs_separate_plain": plain_ms / batch_ms,
            "speedup_vs_separate_fused": fused_ms / batch_ms,
-           "tiles": plan.tiles, "launches_per_run": 4,
+           "tiles": plan.tiles, "launches_per_run": launches_per_run,
            "autotuned_buckets": len(table), "autotune_s": tune_s,
            "bit_identical_to_separate": bool(same)}
     plan.close()

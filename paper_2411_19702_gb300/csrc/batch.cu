@@ -8,9 +8,10 @@
 //   vars   the per-variable epilogue terms, same indexing as v;
 //   tables PackJob[] (one per operand), variable ranges and MiParams per
 //          operand, GramJob[] (one per job) and the flat GramTile[] list.
-// The graph runs: zero(v) -> grouped pack -> grouped mi_vars -> one
-// persistent Gram launch over all tiles (descending per-tile cost, so the
-// round-robin assignment of the persistent CTAs ends with the small tiles).
+// The graph runs: zero(v) -> grouped pack -> grouped mi_vars -> the
+// persistent Gram over all tiles: large jobs on CTA pairs in one launch, the
+// rest on single-CTA tiles in a second (each in descending per-tile cost, so
+// the persistent CTAs end with the small tiles).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -30,7 +31,8 @@ struct gbmi_batch {
     std::vector<int> pack_of_x, pack_of_y;   // pack-job index of each job's X and Y
     int64_t total_rows = 0, total_vars = 0, total_ctas = 0;
     int64_t num_tiles = 0;
-    int grid = 0;
+    int64_t pair_tiles = 0;   // tiles [0, pair_tiles) run on CTA pairs (256 x 256)
+    int grid = 0, pair_grid = 0;
     gbmi::OperandMaps maps;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -94,15 +96,24 @@ gbmi_status enqueue(gbmi_batch* b, cudaStream_t s, unsigned int* err) {
     GramLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.jobs = static_cast<const GramJob*>(b->gramjobs.p);
-    L.tiles = static_cast<const GramTile*>(b->tiles.p);
-    L.num_tiles = static_cast<int>(b->num_tiles);
     L.mode = kTcModeMI;
     L.err = err;
     L.timeout_ns = rt::g_opt.timeout_ns;
     L.debug_flags = rt::g_opt.debug_flags;
-    L.counter = static_cast<unsigned int*>(b->sched.p);
-    GBMI_CUDA(cudaMemsetAsync(b->sched.p, 0, sizeof(unsigned int), s), "batch tile counter");
-    GBMI_CUDA(launch_gram_tc(b->maps, L, b->grid, s), "batch gram");
+    if (b->pair_tiles > 0) {   // the large jobs, on CTA pairs
+        GramLaunch P = L;
+        P.tiles = static_cast<const GramTile*>(b->tiles.p);
+        P.num_tiles = static_cast<int>(b->pair_tiles);
+        P.pair = 1;
+        GBMI_CUDA(launch_gram_tc(b->maps, P, b->pair_grid, s), "batch gram (pairs)");
+    }
+    if (b->num_tiles > b->pair_tiles) {
+        L.tiles = static_cast<const GramTile*>(b->tiles.p) + b->pair_tiles;
+        L.num_tiles = static_cast<int>(b->num_tiles - b->pair_tiles);
+        L.counter = static_cast<unsigned int*>(b->sched.p);
+        GBMI_CUDA(cudaMemsetAsync(b->sched.p, 0, sizeof(unsigned int), s), "batch tile counter");
+        GBMI_CUDA(launch_gram_tc(b->maps, L, b->grid, s), "batch gram");
+    }
     return GBMI_OK;
 }
 
@@ -215,19 +226,37 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
         g.vb = varsb + reinterpret_cast<uintptr_t>(g.vb) / sizeof(MiVar);
     }
 
-    // ---- tiles: jobs by descending per-tile cost, each job in its own order
+    // ---- tiles.  Jobs whose both sides span at least kPairMinN variables run
+    // on CTA pairs (256 x 256 tiles, half the operand bytes per SM per MMA) in
+    // a first launch; the rest on single-CTA tiles of their own width in a
+    // second.  Within each launch, jobs by descending per-tile cost, each job
+    // in its own order.
+    constexpr int64_t kPairMinN = 768;
+    std::vector<char> pair_job(static_cast<size_t>(k), 0);
+    const bool pairs_ok = rt::g_opt.pair != 0 && c.pair_clusters > 0 && rt::g_opt.tile_n == 0;
+    for (int i = 0; i < k; ++i) {
+        GramJob& g = b->hgram[i];
+        if (pairs_ok && (rt::g_opt.pair == 2 || (g.n_a >= kPairMinN && g.n_b >= kPairMinN))) {
+            pair_job[i] = 1;
+            g.bn = kTcBNMax;
+        }
+    }
+    auto tile_m = [&](int i) { return pair_job[i] ? 2 * kTcBM : kTcBM; };
     std::vector<int> order(k);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (pair_job[x] != pair_job[y]) return pair_job[x] > pair_job[y];
         const GramJob& a = b->hgram[x];
         const GramJob& c2 = b->hgram[y];
-        return static_cast<int64_t>(a.k_blocks) * (kTcBM + a.bn) >
-               static_cast<int64_t>(c2.k_blocks) * (kTcBM + c2.bn);
+        return static_cast<int64_t>(a.k_blocks) * (tile_m(x) + a.bn) >
+               static_cast<int64_t>(c2.k_blocks) * (tile_m(y) + c2.bn);
     });
-    int64_t ntiles = 0;
+    int64_t ntiles = 0, npair = 0;
     for (int i = 0; i < k; ++i) {
         const GramJob& g = b->hgram[i];
-        ntiles += gram_tile_count(g.n_a, g.n_b, g.bn, g.symmetric != 0);
+        const int64_t t = gram_tile_count(g.n_a, g.n_b, g.bn, g.symmetric != 0, tile_m(i));
+        ntiles += t;
+        if (pair_job[i]) npair += t;
     }
     if (ntiles > 0x7FFFFFFF) {
         release_plan(b);
@@ -239,11 +268,13 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
     for (int i : order) {
         const GramJob& g = b->hgram[i];
         gram_tiles(i, g.n_a, g.n_b, g.bn, g.symmetric != 0, rt::g_opt.group_cols,
-                   tiles.data() + pos);
-        pos += gram_tile_count(g.n_a, g.n_b, g.bn, g.symmetric != 0);
+                   tiles.data() + pos, tile_m(i));
+        pos += gram_tile_count(g.n_a, g.n_b, g.bn, g.symmetric != 0, tile_m(i));
     }
     b->num_tiles = ntiles;
-    b->grid = rt::grid_for(c, ntiles);
+    b->pair_tiles = npair;
+    b->grid = rt::grid_for(c, ntiles - npair);
+    b->pair_grid = 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, npair));
 
     st = upload(b->packjobs, b->hpack.data(), b->hpack.size() * sizeof(PackJob), "batch pack table");
     if (st == GBMI_OK)
@@ -291,6 +322,12 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
     return GBMI_OK;
 }
 
+// Kernels in the plan's graph: zero, grouped pack, grouped per-variable
+// terms, and one or two Gram launches.
+uint64_t launches_per_run(const gbmi_batch* b) {
+    return 3u + (b->pair_tiles > 0 ? 1u : 0u) + (b->num_tiles > b->pair_tiles ? 1u : 0u);
+}
+
 gbmi_status run(gbmi_batch* b) {
     int dev = 0;
     GBMI_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -298,7 +335,7 @@ gbmi_status run(gbmi_batch* b) {
     cudaEvent_t ev0 = rt::prof_begin(rt::g_stream);
     GBMI_CUDA(cudaGraphLaunch(b->exec, rt::g_stream), "cudaGraphLaunch");
     rt::prof_end("batch_graph", ev0, rt::g_stream);
-    rt::g_launches.fetch_add(4, std::memory_order_relaxed);
+    rt::g_launches.fetch_add(launches_per_run(b), std::memory_order_relaxed);
     return GBMI_OK;
 }
 

@@ -124,6 +124,7 @@ struct Slot {
 struct gbmi_server {
     int device = 0;
     int sm_count = 0;
+    int pair_clusters = 0;
     int max_batch = 64;
     gbmi::rt::DevBuf mem;
     gbmi::Arena arena;
@@ -233,9 +234,13 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
         pj.push_back(j);
     }
     std::vector<GramJob> gj;
+    std::vector<char> pair_job;
     std::vector<int64_t> order(tickets.size());
     std::iota(order.begin(), order.end(), 0);
-    int64_t ntiles = 0;
+    int64_t ntiles = 0, npair = 0;
+    // requests whose both sides span at least 768 variables run on CTA pairs
+    constexpr int64_t kPairMinN = 768;
+    const bool pairs_ok = rt::g_opt.pair != 0 && S->pair_clusters > 0 && rt::g_opt.tile_n == 0;
     for (int64_t t : tickets) {
         const Request& r = S->reqs[t];
         const Dataset& da = S->datasets[r.a];
@@ -262,20 +267,28 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
         g.out_f = reinterpret_cast<float*>(at(S, r.off_out));
         g.ld_out = r.n_b;
         g.mp = rt::mi_params_plain(r.m, 0, nullptr);
+        const bool pj =
+            pairs_ok && (rt::g_opt.pair == 2 || (r.n_a >= kPairMinN && r.n_b >= kPairMinN));
+        if (pj) g.bn = kTcBNMax;
         gj.push_back(g);
-        ntiles += gram_tile_count(r.n_a, r.n_b, g.bn, sym);
+        pair_job.push_back(pj ? 1 : 0);
+        const int64_t nt = gram_tile_count(r.n_a, r.n_b, g.bn, sym, pj ? 2 * kTcBM : kTcBM);
+        ntiles += nt;
+        if (pj) npair += nt;
     }
+    auto tile_m = [&](int64_t i) { return pair_job[i] ? 2 * kTcBM : kTcBM; };
     std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
-        return static_cast<int64_t>(gj[x].k_blocks) * (kTcBM + gj[x].bn) >
-               static_cast<int64_t>(gj[y].k_blocks) * (kTcBM + gj[y].bn);
+        if (pair_job[x] != pair_job[y]) return pair_job[x] > pair_job[y];
+        return static_cast<int64_t>(gj[x].k_blocks) * (tile_m(x) + gj[x].bn) >
+               static_cast<int64_t>(gj[y].k_blocks) * (tile_m(y) + gj[y].bn);
     });
     std::vector<GramTile> tiles(static_cast<size_t>(ntiles));
     int64_t pos = 0;
     for (int64_t i : order) {
         const GramJob& g = gj[i];
         gram_tiles(static_cast<int>(i), g.n_a, g.n_b, g.bn, g.symmetric != 0, rt::g_opt.group_cols,
-                   tiles.data() + pos);
-        pos += gram_tile_count(g.n_a, g.n_b, g.bn, g.symmetric != 0);
+                   tiles.data() + pos, tile_m(i));
+        pos += gram_tile_count(g.n_a, g.n_b, g.bn, g.symmetric != 0, tile_m(i));
     }
 
     // device tables through the slot's pinned staging buffer
@@ -316,15 +329,29 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
     GramLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.jobs = static_cast<const GramJob*>(sl.djobs.p);
-    L.tiles = static_cast<const GramTile*>(sl.dtiles.p);
-    L.num_tiles = static_cast<int>(ntiles);
     L.mode = kTcModeMI;
-    L.counter = ctrl;
     L.err = ctrl + 1;
     L.timeout_ns = rt::g_opt.timeout_ns;
-    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(S->sm_count, ntiles)));
-    GBMI_CUDA(launch_gram_tc(S->maps, L, grid, sl.s), "serve gram");
-    rt::g_launches.fetch_add(2 + sl.packs.size(), std::memory_order_relaxed);
+    uint64_t launches = sl.packs.size() + (sl.packs.empty() ? 0 : 1);
+    if (npair > 0) {   // the large requests, on CTA pairs
+        GramLaunch Pl = L;
+        Pl.tiles = static_cast<const GramTile*>(sl.dtiles.p);
+        Pl.num_tiles = static_cast<int>(npair);
+        Pl.pair = 1;
+        const int pgrid = 2 * static_cast<int>(std::min<int64_t>(S->pair_clusters, npair));
+        GBMI_CUDA(launch_gram_tc(S->maps, Pl, pgrid, sl.s), "serve gram (pairs)");
+        ++launches;
+    }
+    if (ntiles > npair) {
+        L.tiles = static_cast<const GramTile*>(sl.dtiles.p) + npair;
+        L.num_tiles = static_cast<int>(ntiles - npair);
+        L.counter = ctrl;
+        const int grid = static_cast<int>(
+            std::max<int64_t>(1, std::min<int64_t>(S->sm_count, ntiles - npair)));
+        GBMI_CUDA(launch_gram_tc(S->maps, L, grid, sl.s), "serve gram");
+        ++launches;
+    }
+    rt::g_launches.fetch_add(launches, std::memory_order_relaxed);
     GBMI_CUDA(cudaMemcpyAsync(sl.pin_err, ctrl + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost,
                               sl.s),
               "serve error word");
@@ -470,6 +497,7 @@ gbmi_status create(int64_t budget, int max_batch, gbmi_server** out) {
     gbmi_server* S = new gbmi_server();
     S->max_batch = max_batch;
     S->sm_count = cp->sm_count;
+    S->pair_clusters = cp->pair_clusters;
     cudaGetDevice(&S->device);
     const size_t bytes = static_cast<size_t>(budget) & ~static_cast<size_t>(255);
     gbmi_status st = rt::ensure(S->mem, bytes, "server arena");

@@ -104,3 +104,18 @@ def test_autotuner_installs_choices_and_keeps_results():
     gbmi.sync()
     assert torch.equal(got, ref)
     gbmi.tuner_clear()
+
+
+def test_batch_on_cta_pairs_matches_single_calls():
+    """Every job's Gram on CTA pairs (forced); the default rule puts the large jobs there."""
+    Xs, Ys = _problems(400)
+    gbmi.set_option(gbmi.OPT_PAIR, 2)
+    try:
+        b = gbmi.Batch(Xs, Ys)
+        outs = b.run()
+        gbmi.sync()
+        for X, Y, got in zip(Xs, Ys, outs):
+            assert torch.equal(got, _alone(X, Y))
+        b.close()
+    finally:
+        gbmi.set_option(gbmi.OPT_PAIR, 1)

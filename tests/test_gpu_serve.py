@@ -137,3 +137,21 @@ def test_remove_dataset_after_its_requests():
         srv.release(t3)
         with pytest.raises(gbmi.GbmiError):
             srv.submit(a, b)
+
+
+def test_requests_on_cta_pairs_match_single_calls():
+    """Every request's Gram on CTA pairs (forced), then large ones only (default rule)."""
+    Xs = _datasets(70) + [_rand(2000, 1000, 71), _rand(2000, 800, 72)]
+    reqs = REQUESTS + [(10, None), (10, 11), (11, None)]
+    for mode in (2, 1):
+        gbmi.set_option(gbmi.OPT_PAIR, mode)
+        try:
+            with gbmi.Server(1 << 30, max_batch=8) as srv:
+                ids = [srv.add_dataset(X) for X in Xs]
+                tickets = [srv.submit(ids[a], None if b is None else ids[b]) for a, b in reqs]
+                for (a, b), t in zip(reqs, tickets):
+                    got, _ = srv.wait(t, timeout_ms=60_000)
+                    assert torch.equal(got, _alone(Xs[a], None if b is None else Xs[b]))
+                    srv.release(t)
+        finally:
+            gbmi.set_option(gbmi.OPT_PAIR, 1)
