@@ -401,6 +401,202 @@ gbmi_status counts_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n
                     m, kTcModeCounts, L.direct ? &L.maps : nullptr);
 }
 
+// Resources of the host-buffer pipeline (created once per device context).
+gbmi_status pipeline_resources(DeviceCtx& c, int events, int panels) {
+    if (c.copy_stream == nullptr)
+        GBMI_CUDA(cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking), "copy stream");
+    while (static_cast<int>(c.events.size()) < events) {
+        cudaEvent_t e;
+        GBMI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        c.events.push_back(e);
+    }
+    if (c.hflags_cap < panels) {
+        if (c.hflags != nullptr) cudaFreeHost(c.hflags);
+        c.hflags = nullptr;
+        c.hflags_cap = 0;
+        void* h = nullptr;
+        GBMI_CUDA(cudaHostAlloc(&h, static_cast<size_t>(panels) * 4, cudaHostAllocMapped),
+                  "mapped panel flags");
+        c.hflags = static_cast<unsigned int*>(h);
+        void* d = nullptr;
+        GBMI_CUDA(cudaHostGetDevicePointer(&d, h, 0), "cudaHostGetDevicePointer");
+        c.dflags = static_cast<unsigned int*>(d);
+        c.hflags_cap = panels;
+    }
+    return ensure(c.panel, static_cast<size_t>(panels) * 8, "panel counters");
+}
+
+// Host buffers, fused tensor-core path, pipelined:
+//   X (and Y) go up in row chunks on a copy stream, each chunk packed as soon
+//   as it lands (the pack hides under the upload);
+//   one Gram launch runs the tiles in panel-major order (row panels of
+//   panel_blocks tile rows), and the epilogue flags each finished panel in
+//   mapped host memory; the host copies a panel's rows down as soon as it and
+//   every earlier panel are flagged (rows of panel p are written only by
+//   tiles of panels <= p), so the download overlaps the rest of the Gram.
+gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int64_t m,
+                           int64_t n1, int64_t n2, float* out, bool sym) {
+    TcLayout L;
+    L.direct = false;
+    L.kb = pack_ld(m) / kTcBK;
+    L.rows_a = pack_rows(n1);
+    L.rows_b = sym ? 0 : pack_rows(n2);
+    L.total_rows = L.kb * (L.rows_a + L.rows_b);
+    if (L.total_rows >= (int64_t{1} << 31))
+        return fail(GBMI_ERR_ARG, "packed operands exceed 2^31 rows of 128 samples");
+    const size_t ob = static_cast<size_t>(n1) * n2 * 4;
+    GBMI_TRY(ensure(c.P, static_cast<size_t>(L.total_rows) * kTcBK, "FP8 operand"));
+    GBMI_TRY(ensure(c.Xs, static_cast<size_t>(m) * n1, "input staging"));
+    GBMI_TRY(ensure(c.va, static_cast<size_t>(n1) * 4, "column counts"));
+    if (!sym) {
+        GBMI_TRY(ensure(c.Ys, static_cast<size_t>(m) * n2, "input staging"));
+        GBMI_TRY(ensure(c.vb, static_cast<size_t>(n2) * 4, "column counts"));
+    }
+    GBMI_TRY(ensure(c.outs, ob, "output staging"));
+
+    // tiles in panel-major order
+    const int bn_single = rt::choose_bn(m, n1, n2, sym);
+    const bool pair = use_pair(c, n1, n2, sym, bn_single);
+    const int bm = pair ? 2 * kTcBM : kTcBM;
+    const int bn = pair ? kTcBNMax : bn_single;
+    const int64_t TI = (n1 + bm - 1) / bm, TJ = (n2 + bn - 1) / bn;
+    const int64_t pblocks = std::max<int64_t>(1, (TI + 7) / 8);   // about eight panels
+    const int64_t panels = (TI + pblocks - 1) / pblocks;
+    const int group = std::max(1, g_opt.group_cols);
+    std::vector<GramTile> tiles;
+    std::vector<unsigned int> target(static_cast<size_t>(panels), 0);
+    for (int64_t p = 0; p < panels; ++p) {
+        const int64_t I0 = p * pblocks, I1 = std::min(TI, I0 + pblocks);
+        for (int64_t g0 = 0; g0 < TJ; g0 += group)
+            for (int64_t I = I0; I < I1; ++I)
+                for (int64_t J = g0; J < std::min<int64_t>(TJ, g0 + group); ++J) {
+                    if (sym && I * bm > J * bn + bn - 1) continue;
+                    tiles.push_back(GramTile{0, static_cast<int32_t>(I), static_cast<int32_t>(J), 0});
+                    target[static_cast<size_t>(p)] += pair ? 2 * 8 : 8;   // epilogue warps per tile
+                }
+    }
+    if (tiles.size() > 0x7FFFFFFFu) return fail(GBMI_ERR_ARG, "too many tiles");
+    const int64_t R = std::max<int64_t>(kTcBK * 64, round_up((m + 7) / 8, kTcBK));   // chunk rows
+    const int chunks = static_cast<int>((m + R - 1) / R) * (sym ? 1 : 2);
+    GBMI_TRY(pipeline_resources(c, chunks, static_cast<int>(panels)));
+    GBMI_TRY(ensure(c.tiles, tiles.size() * sizeof(GramTile), "tile list"));
+    c.tl_na = -1;   // the single-call tile cache no longer holds this buffer's contents
+    cudaStream_t cs = c.copy_stream;
+    unsigned int* counters = static_cast<unsigned int*>(c.panel.p);
+    unsigned int* targets = counters + panels;
+    std::memset(c.hflags, 0, static_cast<size_t>(panels) * 4);
+    GBMI_CUDA(cudaMemcpyAsync(c.tiles.p, tiles.data(), tiles.size() * sizeof(GramTile),
+                              cudaMemcpyHostToDevice, g_stream),
+              "tile list upload");
+    GBMI_CUDA(cudaMemcpyAsync(targets, target.data(), static_cast<size_t>(panels) * 4,
+                              cudaMemcpyHostToDevice, g_stream),
+              "panel targets");
+    GBMI_CUDA(cudaMemsetAsync(counters, 0, static_cast<size_t>(panels) * 4, g_stream),
+              "panel counters");
+
+    // upload in chunks, pack each chunk as it lands
+    int ev = 0;
+    auto upload_pack = [&](const uint8_t* src, uint8_t* stage, int64_t n, uint8_t* P,
+                           int64_t rows_p, int32_t* v) -> gbmi_status {
+        GBMI_LAUNCH(launch_zero_u32(v, n, g_stream), "zero");
+        for (int64_t r0 = 0; r0 < m; r0 += R) {
+            const int64_t rows = std::min(R, m - r0);
+            GBMI_CUDA(cudaMemcpyAsync(stage + r0 * n, src + r0 * n, static_cast<size_t>(rows) * n,
+                                      cudaMemcpyHostToDevice, cs),
+                      "copy in");
+            GBMI_CUDA(cudaEventRecord(c.events[ev], cs), "event");
+            GBMI_CUDA(cudaStreamWaitEvent(g_stream, c.events[ev], 0), "wait chunk");
+            ++ev;
+            PackJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.X = stage + r0 * n;
+            j.m = rows;
+            j.n = n;
+            j.ldx = n;
+            j.P = P + (r0 / kTcBK) * rows_p * kTcBK;
+            j.v = v;
+            j.rows_p = rows_p;
+            j.ldp = pack_ld(rows);
+            GBMI_LAUNCH(launch_pack(j, g_stream), "pack");
+        }
+        return GBMI_OK;
+    };
+    uint8_t* P = static_cast<uint8_t*>(c.P.p);
+    GBMI_TRY(upload_pack(X, static_cast<uint8_t*>(c.Xs.p), n1, P, L.rows_a,
+                         static_cast<int32_t*>(c.va.p)));
+    if (!sym)
+        GBMI_TRY(upload_pack(Y, static_cast<uint8_t*>(c.Ys.p), n2, P + L.kb * L.rows_a * kTcBK,
+                             L.rows_b, static_cast<int32_t*>(c.vb.p)));
+
+    MiParams mp;
+    GBMI_TRY(rt::mi_params(c, m, &mp));
+    const MiVar *va = nullptr, *vb = nullptr;
+    GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.va.p), n1, mp, c.ha, &va));
+    if (sym)
+        vb = va;
+    else
+        GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.vb.p), n2, mp, c.hb, &vb));
+
+    OperandMaps maps;
+    if (!make_operand_maps(&maps, P, L.total_rows))
+        return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    GramLaunch G;
+    std::memset(&G, 0, sizeof(G));
+    G.job0 = tc_job(L, m, n1, n2, sym, bn, va, vb, mp, static_cast<float*>(c.outs.p), nullptr);
+    G.job0.bn = bn;
+    G.tiles = static_cast<const GramTile*>(c.tiles.p);
+    G.num_tiles = static_cast<int>(tiles.size());
+    G.mode = kTcModeMI;
+    G.err = static_cast<unsigned int*>(c.err.p);
+    G.timeout_ns = g_opt.timeout_ns;
+    G.debug_flags = g_opt.debug_flags;
+    G.pair = pair ? 1 : 0;
+    GBMI_TRY(ensure(c.sched, 256, "tile counter"));
+    G.counter = static_cast<unsigned int*>(c.sched.p);
+    G.panel_done = counters;
+    G.panel_target = targets;
+    G.host_flags = c.dflags;
+    G.panel_blocks = static_cast<int>(pblocks);
+    const int grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, G.num_tiles))
+                          : rt::grid_for(c, G.num_tiles);
+    GBMI_CUDA(cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
+    GBMI_LAUNCH(launch_gram_tc(maps, G, grid, g_stream), "gram_tc_fused_mi");
+
+    // download each panel once it and every earlier panel are complete; if
+    // the launch ends first (or fails), the rest follows it on the stream
+    const volatile unsigned int* flags = c.hflags;
+    const float* outs = static_cast<const float*>(c.outs.p);
+    bool launch_over = false, ordered = false;
+    for (int64_t p = 0; p < panels; ++p) {
+        const int64_t r0 = p * pblocks * bm;
+        const int64_t r1 = std::min(n1, (p + 1) * pblocks * bm);
+        for (uint64_t it = 0; !launch_over && flags[p] == 0u; ++it) {
+            if ((it & 1023u) == 1023u) {
+                const cudaError_t q = cudaStreamQuery(g_stream);
+                if (q != cudaErrorNotReady) launch_over = true;   // done, or failed
+            }
+        }
+        if (launch_over && !ordered) {   // the remaining copies follow the launch
+            GBMI_CUDA(cudaEventRecord(c.events[0], g_stream), "event");
+            GBMI_CUDA(cudaStreamWaitEvent(cs, c.events[0], 0), "wait launch");
+            ordered = true;
+        }
+        GBMI_CUDA(cudaMemcpyAsync(out + r0 * n2, outs + r0 * n2,
+                                  static_cast<size_t>(r1 - r0) * n2 * 4, cudaMemcpyDeviceToHost,
+                                  cs),
+                  "copy out");
+    }
+    GBMI_CUDA(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
+    GBMI_CUDA(cudaStreamSynchronize(g_stream), "cudaStreamSynchronize");
+    unsigned int err = 0;
+    GBMI_CUDA(cudaMemcpy(&err, c.err.p, sizeof(err), cudaMemcpyDeviceToHost), "read error word");
+    if (err != 0) {
+        cudaMemset(c.err.p, 0, sizeof(err));
+        return error_word_status(err);
+    }
+    return GBMI_OK;
+}
+
 gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
                       float* out, bool sym) {
     if (X == nullptr || out == nullptr || (!sym && Y == nullptr))
@@ -409,6 +605,8 @@ gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
     DeviceCtx* cp = nullptr;
     GBMI_TRY(rt::get_ctx(&cp));
     DeviceCtx& c = *cp;
+    if (choose_path(GBMI_PATH_AUTO, m, n1, n2) == GBMI_PATH_FUSED && !g_opt.direct)
+        return host_pipelined(c, X, Y, m, n1, n2, out, sym);
     const size_t xb = static_cast<size_t>(m) * n1, yb = static_cast<size_t>(m) * n2;
     const size_t ob = static_cast<size_t>(n1) * n2 * 4;
     GBMI_TRY(ensure(c.Xs, xb, "input staging"));
@@ -878,8 +1076,12 @@ gbmi_status gbmi_shutdown(void) {
         cudaDeviceSynchronize();
         rt::release(c->sched);
         for (DevBuf* b : {&c->P, &c->Ba, &c->Bb, &c->va, &c->vb, &c->ha, &c->hb, &c->counts,
-                          &c->T, &c->err, &c->tiles, &c->Xs, &c->Ys, &c->outs, &c->flag})
+                          &c->T, &c->err, &c->tiles, &c->Xs, &c->Ys, &c->outs, &c->flag,
+                          &c->panel})
             rt::release(*b);
+        for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+        if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+        if (c->hflags) cudaFreeHost(c->hflags);
         *c = DeviceCtx();
     }
     cudaSetDevice(cur);

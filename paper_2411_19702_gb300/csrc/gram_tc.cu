@@ -589,6 +589,18 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                 }
             }
         }
+        if (L.panel_done != nullptr) {   // this warp's stores of the tile are done
+            __syncwarp();
+            __threadfence();
+            if (lane == 0) {
+                const int p = tile.I / L.panel_blocks;
+                const unsigned int old = atomicAdd(L.panel_done + p, 1u);
+                if (old + 1u == L.panel_target[p]) {
+                    __threadfence_system();
+                    *reinterpret_cast<volatile unsigned int*>(L.host_flags + p) = 1u;
+                }
+            }
+        }
         ptx::tc_fence_before();
         if constexpr (kPair) {   // one arrival per warp, on CTA 0's barrier
             __syncwarp();

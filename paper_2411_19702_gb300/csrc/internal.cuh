@@ -170,6 +170,15 @@ struct GramLaunch {
     // launch), so the tiles in flight are always a contiguous window of the
     // list.  Null: static round-robin (tile blockIdx.x + k * gridDim.x).
     unsigned int* counter;
+    // Panel completion (or null): tile row block I belongs to panel
+    // I / panel_blocks; every epilogue warp that finishes a tile adds 1 to
+    // panel_done[panel], and the warp that brings it to panel_target[panel]
+    // sets host_flags[panel] = 1 (mapped host memory, after a system fence),
+    // so the host can copy the panel's rows while later panels compute.
+    unsigned int* panel_done;
+    const unsigned int* panel_target;
+    unsigned int* host_flags;
+    int panel_blocks;
 };
 
 // TMA descriptors of a K-block-major operand buffer of total_rows rows of 128

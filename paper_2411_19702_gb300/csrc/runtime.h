@@ -43,6 +43,14 @@ struct DeviceCtx {
     int64_t tl_na = -1, tl_nb = -1;
     int tl_sym = -1, tl_group = -1, tl_bn = -1, tl_bm = -1;
     int pair_clusters = 0;   // CTA pairs of the pair Gram kernel resident at once
+    // host-buffer pipeline: copy stream, chunk events, panel counters / targets
+    // and mapped host flags of panel completion
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> events;
+    DevBuf panel;
+    unsigned int* hflags = nullptr;   // mapped pinned host memory
+    unsigned int* dflags = nullptr;   // its device address
+    int hflags_cap = 0;
     std::vector<GramTile> tl_host;
 };
 

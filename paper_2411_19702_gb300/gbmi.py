@@ -270,29 +270,48 @@ def validate_binary(X) -> bool:
     return True
 
 
-def mi_all_pairs_host(X, out=None):
-    """Host-buffer call: X is a numpy/torch CPU uint8 array; returns a CPU float32 array."""
+def _host_array(A, dtype, name):
+    """(object, pointer) of a contiguous host array: numpy, or a torch CPU tensor."""
     import numpy as np
-    Xn = np.ascontiguousarray(X, dtype=np.uint8) if not hasattr(X, "data_ptr") else X
-    m, n = Xn.shape
+    if hasattr(A, "data_ptr"):
+        if A.is_cuda:
+            raise TypeError(f"{name} must be in host memory")
+        A = A.contiguous()
+        return A, A.data_ptr()
+    A = np.ascontiguousarray(A, dtype=dtype)
+    return A, A.ctypes.data
+
+
+def mi_all_pairs_host(X, out=None):
+    """Host-buffer call: X is a numpy array or torch CPU tensor (uint8, m x n); out
+    (n x n float32, page-locked for the fastest copies) is allocated if None."""
+    import numpy as np
+    X, xp = _host_array(X, np.uint8, "X")
+    m, n = X.shape
     if out is None:
         out = np.empty((n, n), dtype=np.float32)
-    xp = Xn.data_ptr() if hasattr(Xn, "data_ptr") else Xn.ctypes.data
-    op = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
-    lib = load()
-    _check(lib.mi_all_pairs_host(xp, m, n, op))
+    if tuple(out.shape) != (n, n):
+        raise ValueError(f"out must be {n} x {n}")
+    out, op = _host_array(out, np.float32, "out")
+    _check(load().mi_all_pairs_host(xp, m, n, op))
     return out
 
 
 def mi_cross_host(X, Y, out=None):
+    """Host-buffer cross MI between the columns of X (m x n1) and Y (m x n2)."""
     import numpy as np
-    Xn = np.ascontiguousarray(X, dtype=np.uint8)
-    Yn = np.ascontiguousarray(Y, dtype=np.uint8)
-    m, n1 = Xn.shape
-    n2 = Yn.shape[1]
+    X, xp = _host_array(X, np.uint8, "X")
+    Y, yp = _host_array(Y, np.uint8, "Y")
+    m, n1 = X.shape
+    if Y.shape[0] != m:
+        raise ValueError("X and Y must have the same number of samples")
+    n2 = Y.shape[1]
     if out is None:
         out = np.empty((n1, n2), dtype=np.float32)
-    _check(load().mi_cross_host(Xn.ctypes.data, Yn.ctypes.data, m, n1, n2, out.ctypes.data))
+    if tuple(out.shape) != (n1, n2):
+        raise ValueError(f"out must be {n1} x {n2}")
+    out, op = _host_array(out, np.float32, "out")
+    _check(load().mi_cross_host(xp, yp, m, n1, n2, op))
     return out
 
 
