@@ -105,6 +105,8 @@ gbmi_status enqueue(gbmi_batch* b, cudaStream_t s, unsigned int* err) {
         P.tiles = static_cast<const GramTile*>(b->tiles.p);
         P.num_tiles = static_cast<int>(b->pair_tiles);
         P.pair = 1;
+        P.counter = static_cast<unsigned int*>(b->sched.p);
+        GBMI_CUDA(cudaMemsetAsync(b->sched.p, 0, sizeof(unsigned int), s), "batch tile counter");
         GBMI_CUDA(launch_gram_tc(b->maps, P, b->pair_grid, s), "batch gram (pairs)");
     }
     if (b->num_tiles > b->pair_tiles) {

@@ -38,7 +38,9 @@
 // The producer takes the CTA's next tile from a shared atomic counter
 // (dynamic order: the tiles in flight are always a contiguous window of the
 // list, whatever their lengths) or from the static round-robin sequence, and
-// hands its id to the MMA thread and the epilogue warps through an 8-entry
+// hands its id to the MMA thread and the epilogue warps (in a CTA pair, also
+// to the partner's epilogue warps, by a cluster store and a remote arrive;
+// their slot releases come back to CTA 0) through an 8-entry
 // shared-memory queue (queue full / queue empty mbarriers; -1 ends the run).
 //
 // Every mbarrier wait is bounded (timeout_ns from its start, %globaltimer).
@@ -138,38 +140,15 @@ __device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
 // ------------------------------------------------------------------ producer
 // Next tile of this CTA: from the shared counter (dynamic order) or the static
 // round-robin sequence.
-// A CTA pair takes the static sequence of its cluster (both CTAs see the same).
+// Next tile of this CTA (of CTA 0 of a pair): from the shared counter (dynamic
+// order) or the static sequence of the CTA (of the cluster).
 template <bool kPair>
 __device__ __forceinline__ int next_tile(const GramLaunch& L, int s) {
-    if constexpr (kPair) {
+    if (L.counter != nullptr) return static_cast<int>(atomicAdd(L.counter, 1u));
+    if constexpr (kPair)
         return static_cast<int>(ptx::cluster_id_x() + s * ptx::nclusters_x());
-    } else {
-        if (L.counter != nullptr) return static_cast<int>(atomicAdd(L.counter, 1u));
+    else
         return blockIdx.x + s * gridDim.x;
-    }
-}
-
-// Second CTA of a pair: no copies (CTA 0 loads both CTAs' halves), only the
-// tile ids for its own epilogue warps.
-__device__ void run_feeder(const Smem<true>& sm, const GramLaunch& L) {
-    int qslot = 0;
-    uint32_t qphase = 0;
-    for (int s = 0;; ++s) {
-        const int t = next_tile<true>(L, s);
-        if (!ptx::mbar_wait_bounded(sm.qempty(qslot), qphase ^ 1u, L.timeout_ns,
-                                    sm.abort_flag())) {
-            raise_abort(sm, L.err, kErrTimeoutLoad);
-            break;
-        }
-        const int tid = t < L.num_tiles ? t : -1;
-        sm.queue()[qslot] = tid;
-        ptx::mbar_arrive(sm.qfull(qslot));
-        if (++qslot == kQ) {
-            qslot = 0;
-            qphase ^= 1u;
-        }
-        if (tid < 0) break;
-    }
 }
 
 template <bool kPair>
@@ -197,6 +176,12 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         const int tid = t < L.num_tiles ? t : -1;
         sm.queue()[qslot] = tid;
         ptx::mbar_arrive(sm.qfull(qslot));
+        if constexpr (kPair) {   // the partner CTA's epilogue takes the same tile
+            ptx::st_cluster_u32(
+                ptx::mapa_shared(ptx::smem_u32(const_cast<int*>(sm.queue() + qslot)), 1u),
+                static_cast<uint32_t>(tid));
+            ptx::mbar_arrive_cluster(ptx::mapa_shared(sm.qfull(qslot), 1u));
+        }
         if (++qslot == kQ) {
             qslot = 0;
             qphase ^= 1u;
@@ -414,13 +399,20 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
     int qslot = 0;
     uint32_t qphase = 0;
     for (;;) {
-        if (!ptx::mbar_wait_bounded(sm.qfull(qslot), qphase, L.timeout_ns, sm.abort_flag())) {
+        // pair: CTA 0's producer fills both CTAs' queues (cluster-scope acquire)
+        if (!ptx::mbar_wait_bounded<kPair>(sm.qfull(qslot), qphase, L.timeout_ns,
+                                           sm.abort_flag())) {
             raise_abort(sm, L.err, kErrTimeoutEpilogue);
             break;
         }
         const int t = sm.queue()[qslot];
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(sm.qempty(qslot));
+        if (lane == 0) {   // the slot goes back to CTA 0's producer
+            if (kPair && sm.rank != 0)
+                ptx::mbar_arrive_cluster(ptx::mapa_shared(sm.qempty(qslot), 0u));
+            else
+                ptx::mbar_arrive(sm.qempty(qslot));
+        }
         if (++qslot == kQ) {
             qslot = 0;
             qphase ^= 1u;
@@ -646,8 +638,8 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
         ptx::mbar_init(sm.drain(), 1);
         for (int q = 0; q < kQ; ++q) {
             ptx::mbar_init(sm.qfull(q), 1);
-            // MMA thread (CTA 0 only) + one lane per epilogue warp
-            ptx::mbar_init(sm.qempty(q), (lead ? 1 : 0) + kEpiWarps);
+            // MMA thread + one lane per epilogue warp (pair: of both CTAs, on CTA 0)
+            ptx::mbar_init(sm.qempty(q), 1 + (kPair ? 2 : 1) * kEpiWarps);
         }
         *sm.abort_flag() = 0;
         ptx::fence_barrier_init();
@@ -679,12 +671,7 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
     const uint32_t tmem_base = *sm.tmem_holder();
 
     if (warp == 0) {
-        if (lane == 0) {
-            if (lead)
-                run_producer<kPair>(sm, maps, L);
-            else if constexpr (kPair)
-                run_feeder(sm, L);
-        }
+        if (lane == 0 && lead) run_producer<kPair>(sm, maps, L);
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0 && lead) run_mma<kPair>(sm, L, tmem_base);

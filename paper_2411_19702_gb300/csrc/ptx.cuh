@@ -57,16 +57,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// The same with acquire at cluster scope: for a barrier that threads of the
+// other CTA of the cluster arrive on (release.cluster), so that what they
+// stored before arriving is visible after the wait.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait until the phase with the given parity has completed.  Returns false if
 // more than timeout_ns passed since the wait began, or *abort became non-zero,
 // first (the caller then unwinds).
+template <bool kClusterAcquire = false>
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   uint64_t timeout_ns,
                                                   const volatile int* abort) {
-    if (mbar_try_wait(bar, parity)) return true;
+    auto ready = [&]() {
+        return kClusterAcquire ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity);
+    };
+    if (ready()) return true;
     uint64_t t0 = 0;
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (ready()) return true;
         if ((it & 63u) == 0) {
             if (*abort) return false;
             const uint64_t now = globaltimer_ns();

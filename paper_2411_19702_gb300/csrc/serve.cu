@@ -115,7 +115,7 @@ struct Slot {
     void* pin = nullptr;
     size_t pin_cap = 0;
     unsigned int* pin_err = nullptr;
-    int64_t off_ctrl = -1;            // arena: tile counter + error word
+    int64_t off_ctrl = -1;            // arena: tile counter, error word, pair tile counter
 };
 
 }  // namespace
@@ -325,7 +325,7 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
     }
     GBMI_CUDA(cudaEventRecord(sl.packed, sl.s), "serve event");
     unsigned int* ctrl = reinterpret_cast<unsigned int*>(at(S, sl.off_ctrl));
-    GBMI_CUDA(cudaMemsetAsync(ctrl, 0, 2 * sizeof(unsigned int), sl.s), "serve counter");
+    GBMI_CUDA(cudaMemsetAsync(ctrl, 0, 3 * sizeof(unsigned int), sl.s), "serve counter");
     GramLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.jobs = static_cast<const GramJob*>(sl.djobs.p);
@@ -338,6 +338,7 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
         Pl.tiles = static_cast<const GramTile*>(sl.dtiles.p);
         Pl.num_tiles = static_cast<int>(npair);
         Pl.pair = 1;
+        Pl.counter = ctrl + 2;   // its own tile counter (zeroed with the others)
         const int pgrid = 2 * static_cast<int>(std::min<int64_t>(S->pair_clusters, npair));
         GBMI_CUDA(launch_gram_tc(S->maps, Pl, pgrid, sl.s), "serve gram (pairs)");
         ++launches;
