@@ -23,7 +23,8 @@ namespace {
 constexpr int kPackThreads = 256;
 constexpr int kTileR = 128;        // samples per tile
 constexpr int kTileJ = 128;        // variables per CTA
-constexpr int kTilesPerCta = 16;   // sample tiles walked by one CTA (at least)
+constexpr int kTilesPerCta = 16;   // sample tiles walked by one CTA (at most, usually)
+constexpr int64_t kPackCtasTarget = 152 * 8;   // CTAs one job should launch: 2 waves
 
 // 1 in every byte that is non-zero, 0 elsewhere.
 __device__ __forceinline__ uint32_t nz_bytes(uint32_t w) {
@@ -49,17 +50,9 @@ __device__ __forceinline__ void transpose4x4(const uint32_t w0, const uint32_t w
     c3 = __byte_perm(t2, t3, 0x7632);
 }
 
-// 16 bytes starting at any address p, of which the first nvalid (1..16) are
-// kept and the rest zeroed.  Only the 16-byte-aligned granules that hold the
-// bytes [p, p + nvalid) are read, so nothing outside the caller's range is
-// touched, and the bytes are shifted into place with funnel shifts.
-__device__ __forceinline__ uint4 load16_any(const uint8_t* p, int nvalid) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    const int s = static_cast<int>(a & 15);
-    const uint4* g = reinterpret_cast<const uint4*>(a - s);
-    const uint4 g0 = __ldg(g);
-    uint4 g1 = make_uint4(0, 0, 0, 0);
-    if (s + nvalid > 16) g1 = __ldg(g + 1);
+// Bytes [s, s + 16) of the 32 bytes g0:g1 (two consecutive aligned 16-byte
+// granules), of which the first keep (<= 16) are kept and the rest zeroed.
+__device__ __forceinline__ uint4 realign16(const uint4 g0, const uint4 g1, int s, int keep) {
     const uint32_t w[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
     const int q = s >> 2;
     const uint32_t sh = static_cast<uint32_t>(s & 3) * 8u;
@@ -71,11 +64,11 @@ __device__ __forceinline__ uint4 load16_any(const uint8_t* p, int nvalid) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         o[i] = __funnelshift_r(sel[i], sel[i + 1], sh);
-        const int keep = nvalid - 4 * i;   // bytes of this word that are valid
-        if (keep <= 0) {
+        const int k = keep - 4 * i;   // bytes of this word that are valid
+        if (k <= 0) {
             o[i] = 0u;
-        } else if (keep < 4) {
-            o[i] &= (1u << (8 * keep)) - 1u;
+        } else if (k < 4) {
+            o[i] &= (1u << (8 * k)) - 1u;
         }
     }
     return make_uint4(o[0], o[1], o[2], o[3]);
@@ -93,6 +86,7 @@ __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
 // sits in shared memory with its 16-byte chunks XOR-swizzled by the row's
 // 16-row group (chunk ^ (r / 16) % 8), which keeps both the row-wise fill
 // and the column-wise reads of the transpose free of bank conflicts.
+template <bool kAligned>
 __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, const int64_t by,
                                          uint8_t* S) {
     const int t = threadIdx.x;
@@ -110,27 +104,56 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
     int colsum[4] = {0, 0, 0, 0};
     const uint32_t* S32 = reinterpret_cast<const uint32_t*>(S);
 
-    // the next tile's 16-byte loads are issued before the current tile is
-    // transposed and stored, so they overlap that work
-    // (rows of X that are not 16-byte aligned go through load16_any)
+    // The next tile's loads are issued before the current tile is transposed
+    // and stored, so they are in flight during that work.  Aligned rows: one
+    // 16-byte load per lane and row.  Rows of X that are not 16-byte aligned:
+    // the (at most two) aligned granules that hold each lane's 16 bytes,
+    // realigned only when the tile is written to shared memory; only granules
+    // holding bytes of [j, min(j + 16, n)) are read.
+    // The next tile's loads are issued before the current tile is transposed
+    // and stored, so they are in flight during that work.  Unaligned rows:
+    // each lane reads the (at most two) aligned granules holding its 16 bytes,
+    // all eight loads first, then realigns them (funnel shifts); only granules
+    // holding bytes of [j, min(j + 16, n)) are read.
     uint4 pre[4];
-    auto load_tile = [&](int64_t tile) {
+    auto issue_tile = [&](int64_t tile) {
         const int64_t r0 = tile * kTileR;
+        const int64_t jl = j0 + (t & 7) * 16;
+        if constexpr (kAligned) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t r = r0 + q * 32 + (t >> 3);
-            const int64_t j = j0 + (t & 7) * 16;
-            pre[q] = make_uint4(0, 0, 0, 0);
-            if (r < a.m && j < a.n) {
-                const uint8_t* p = a.X + r * a.ldx + j;
-                if (vec)
-                    pre[q] = __ldg(reinterpret_cast<const uint4*>(p));
-                else
-                    pre[q] = load16_any(p, a.n - j < 16 ? static_cast<int>(a.n - j) : 16);
+            for (int q = 0; q < 4; ++q) {
+                const int64_t r = r0 + q * 32 + (t >> 3);
+                pre[q] = make_uint4(0, 0, 0, 0);
+                if (r < a.m && jl < a.n)
+                    pre[q] = __ldg(reinterpret_cast<const uint4*>(a.X + r * a.ldx + jl));
+            }
+        } else {
+            const int keep_j =
+                jl >= a.n ? 0 : (a.n - jl < 16 ? static_cast<int>(a.n - jl) : 16);
+            uint4 g1[4];
+            uint32_t meta = 0;   // row q: misalignment in bits 8q..8q+3, valid in bit 8q+4
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t r = r0 + q * 32 + (t >> 3);
+                pre[q] = g1[q] = make_uint4(0, 0, 0, 0);
+                if (r < a.m && keep_j > 0) {
+                    const uintptr_t ad = reinterpret_cast<uintptr_t>(a.X + r * a.ldx + jl);
+                    const int s = static_cast<int>(ad & 15);
+                    meta |= static_cast<uint32_t>(s | 16) << (8 * q);
+                    const uint4* g = reinterpret_cast<const uint4*>(ad - s);
+                    pre[q] = __ldg(g);
+                    if (s + keep_j > 16) g1[q] = __ldg(g + 1);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t mq = (meta >> (8 * q)) & 0x1Fu;
+                pre[q] = realign16(pre[q], g1[q], static_cast<int>(mq & 15u),
+                                   mq & 16u ? keep_j : 0);
             }
         }
     };
-    if (tile_begin < tile_end) load_tile(tile_begin);
+    if (tile_begin < tile_end) issue_tile(tile_begin);
 
     for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
         const int64_t r0 = tile * kTileR;
@@ -142,7 +165,7 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
             *reinterpret_cast<uint4*>(S + r * kTileJ + chunk * 16) = pre[q];
         }
         __syncthreads();
-        if (tile + 1 < tile_end) load_tile(tile + 1);
+        if (tile + 1 < tile_end) issue_tile(tile + 1);
 
         // ---- transpose: variables 16 w + 4 vg .. +3, samples 16 sg .. +15
         const int swz = colw ^ (4 * sg);   // rows 16 sg .. +15 share one swizzle
@@ -201,11 +224,13 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
     }
 }
 
+// One instantiation for 16-byte aligned rows, one for the rest.
+template <bool kAligned>
 __global__ void __launch_bounds__(kPackThreads, 4)   // 4 CTAs per SM: loads in flight
 pack_kernel(const PackJob job) {
     __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
     const int64_t c = blockIdx.x;
-    pack_cta(job, c % job.gx, c / job.gx, S);
+    pack_cta<kAligned>(job, c % job.gx, c / job.gx, S);
 }
 
 __global__ void __launch_bounds__(kPackThreads, 4)
@@ -219,7 +244,10 @@ pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs) {
     }
     const PackJob job = jobs[lo];
     const int64_t cl = c - job.cta_begin;
-    pack_cta(job, cl % job.gx, cl / job.gx, S);
+    if (job.vec)
+        pack_cta<true>(job, cl % job.gx, cl / job.gx, S);
+    else
+        pack_cta<false>(job, cl % job.gx, cl / job.gx, S);
 }
 
 __global__ void validate_kernel(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
@@ -307,9 +335,13 @@ colsum_kernel(const uint8_t* __restrict__ X, int64_t m, int64_t n, int64_t rows_
 
 int64_t pack_job_ctas(PackJob& a) {
     const int64_t tiles_total = a.ldp / kTileR;
-    int64_t tpc = kTilesPerCta;
     a.gx = static_cast<int32_t>(a.rows_p / kTileJ);
-    // keep the job's CTA count moderate for very long sample ranges
+    // Tiles per CTA: at most kTilesPerCta, fewer when the job has few column
+    // blocks, so that a job alone still launches about kPackCtasTarget CTAs
+    // (enough loads in flight to stream HBM); more for very long sample ranges,
+    // to keep the CTA count moderate.
+    int64_t tpc = (tiles_total * a.gx + kPackCtasTarget - 1) / kPackCtasTarget;
+    tpc = tpc < 1 ? 1 : (tpc > kTilesPerCta ? kTilesPerCta : tpc);
     while ((tiles_total + tpc - 1) / tpc > (int64_t{1} << 16)) tpc *= 2;
     a.tpc = static_cast<int32_t>(tpc);
     a.vec = (a.ldx % 16 == 0) && (a.n % 16 == 0) &&
@@ -322,7 +354,10 @@ cudaError_t launch_pack(const PackJob& job, cudaStream_t s) {
     PackJob j = job;
     const int64_t ctas = pack_job_ctas(j);
     if (ctas <= 0 || ctas > 0x7FFFFFFF) return cudaErrorInvalidValue;
-    pack_kernel<<<static_cast<unsigned>(ctas), kPackThreads, 0, s>>>(j);
+    if (j.vec)
+        pack_kernel<true><<<static_cast<unsigned>(ctas), kPackThreads, 0, s>>>(j);
+    else
+        pack_kernel<false><<<static_cast<unsigned>(ctas), kPackThreads, 0, s>>>(j);
     return cudaGetLastError();
 }
 
