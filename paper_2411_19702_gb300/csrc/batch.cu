@@ -97,6 +97,7 @@ gbmi_status enqueue(gbmi_batch* b, cudaStream_t s, unsigned int* err) {
     std::memset(&L, 0, sizeof(L));
     L.jobs = static_cast<const GramJob*>(b->gramjobs.p);
     L.mode = kTcModeMI;
+    L.fixup = b->hgram.empty() ? 0 : b->hgram[0].mp.fixup;   // one setting for every job
     L.err = err;
     L.timeout_ns = rt::g_opt.timeout_ns;
     L.debug_flags = rt::g_opt.debug_flags;

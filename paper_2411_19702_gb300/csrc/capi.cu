@@ -143,6 +143,7 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     L.job0 = proto;
     L.job0.bn = bn;
     L.pair = pair ? 1 : 0;
+    L.fixup = proto.mp.fixup;
     L.tiles = static_cast<const GramTile*>(c.tiles.p);
     L.num_tiles = tiles;
     L.err = static_cast<unsigned int*>(c.err.p);
@@ -465,6 +466,10 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
     const int group = std::max(1, g_opt.group_cols);
     std::vector<GramTile> tiles;
     std::vector<unsigned int> target(static_cast<size_t>(panels), 0);
+    MiParams mp;
+    GBMI_TRY(rt::mi_params(c, m, &mp));
+    const unsigned int epi = static_cast<unsigned int>(
+        gram_tc_epilogue_warps(kTcModeMI, mp.fixup) * (pair ? 2 : 1));
     for (int64_t p = 0; p < panels; ++p) {
         const int64_t I0 = p * pblocks, I1 = std::min(TI, I0 + pblocks);
         for (int64_t g0 = 0; g0 < TJ; g0 += group)
@@ -472,7 +477,7 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
                 for (int64_t J = g0; J < std::min<int64_t>(TJ, g0 + group); ++J) {
                     if (sym && I * bm > J * bn + bn - 1) continue;
                     tiles.push_back(GramTile{0, static_cast<int32_t>(I), static_cast<int32_t>(J), 0});
-                    target[static_cast<size_t>(p)] += pair ? 2 * 8 : 8;   // epilogue warps per tile
+                    target[static_cast<size_t>(p)] += epi;   // epilogue warps per tile
                 }
     }
     if (tiles.size() > 0x7FFFFFFFu) return fail(GBMI_ERR_ARG, "too many tiles");
@@ -528,8 +533,6 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
         GBMI_TRY(upload_pack(Y, static_cast<uint8_t*>(c.Ys.p), n2, P + L.kb * L.rows_a * kTcBK,
                              L.rows_b, static_cast<int32_t*>(c.vb.p)));
 
-    MiParams mp;
-    GBMI_TRY(rt::mi_params(c, m, &mp));
     const MiVar *va = nullptr, *vb = nullptr;
     GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.va.p), n1, mp, c.ha, &va));
     if (sym)
@@ -551,6 +554,7 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
     G.timeout_ns = g_opt.timeout_ns;
     G.debug_flags = g_opt.debug_flags;
     G.pair = pair ? 1 : 0;
+    G.fixup = mp.fixup;
     GBMI_TRY(ensure(c.sched, 256, "tile counter"));
     G.counter = static_cast<unsigned int*>(c.sched.p);
     G.panel_done = counters;
@@ -771,6 +775,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
             G.debug_flags = g_opt.debug_flags;
             G.direct = L.direct ? 1 : 0;
             G.pair = pair_panel[p];
+            G.fixup = mp.fixup;
             G.counter = static_cast<unsigned int*>(c.sched.p);
             const int grid =
                 G.pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, G.num_tiles))

@@ -58,16 +58,24 @@ namespace gbmi {
 
 namespace {
 
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + 32 * kEpiWarps;    // 320
+// Kernel-only mode: MI with the FP64 combine compiled out (launched for MI
+// whenever the combine is off, so the epilogue's code stays small).
+constexpr int kTcModeMI32 = 3;
+template <int kMode>
+__host__ __device__ constexpr bool is_mi() { return kMode == kTcModeMI || kMode == kTcModeMI32; }
+// Epilogue warps: 16 (four per TMEM lane quadrant) hide the latency of the
+// per-pair arithmetic; the FP64-combine variant needs too many registers for
+// 576 threads and keeps 8.
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == kTcModeMI ? 8 : 16; }
+__host__ __device__ constexpr int threads_of(int mode) { return 64 + 32 * epi_warps(mode); }
 constexpr int kUmmaK = 32;                       // K per MMA for 8-bit inputs
 constexpr int kABytes = kTcBM * kTcBK;           // 16 KB: 128 rows of A
 constexpr int kAccCols = kTcBNMax;               // TMEM columns per accumulator buffer
 constexpr int kTmemCols = 2 * kAccCols;          // 512: the whole tensor memory
-constexpr int kColsPerWarpMax = kTcBNMax / 2;    // 128
+constexpr size_t kColVarTotal = 32768;           // staged column terms of all epilogue warps
 constexpr int kGroup = 16;                       // accumulator columns per tcgen05.ld
 constexpr int kQ = 8;                            // tile-id queue between the roles
-constexpr size_t kColVarBytes = static_cast<size_t>(kColsPerWarpMax) * sizeof(MiVar);   // 4 KB
+
 // full, empty, tmem full x2, tmem empty x2, drain, queue full x kQ, queue empty x kQ
 constexpr int kNumBarsFor(int stages) { return 2 * stages + 4 + 1 + 2 * kQ; }
 
@@ -81,7 +89,7 @@ struct Plan {
     static constexpr int stage_bytes = kABytes + b_bytes;
     static constexpr int tile_m = kPair ? 2 * kTcBM : kTcBM;   // rows of A per tile
     static constexpr size_t off_colvars = static_cast<size_t>(stages) * stage_bytes;
-    static constexpr size_t off_bars = off_colvars + kEpiWarps * kColVarBytes;
+    static constexpr size_t off_bars = off_colvars + kColVarTotal;
     static constexpr int num_bars = kNumBarsFor(stages);
     static constexpr size_t off_misc = off_bars + num_bars * 8;
     static constexpr size_t off_queue = off_misc + 64;
@@ -97,8 +105,9 @@ struct Smem {
     uint32_t rank;   // CTA rank in the pair (0 when single)
     __device__ uint8_t* a(int s) const { return base + s * P::stage_bytes; }
     __device__ uint8_t* b(int s) const { return base + s * P::stage_bytes + kABytes; }
-    __device__ MiVar* colvars(int e) const {
-        return reinterpret_cast<MiVar*>(base + P::off_colvars + e * kColVarBytes);
+    // column terms of epilogue warp e of nepi (kColVarTotal / nepi bytes each)
+    __device__ MiVar* colvars(int e, int nepi) const {
+        return reinterpret_cast<MiVar*>(base + P::off_colvars + e * (kColVarTotal / nepi));
     }
     __device__ uint64_t* bar(int k) const {
         return reinterpret_cast<uint64_t*>(base + P::off_bars) + k;
@@ -377,7 +386,7 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
 template <int kMode>
 __device__ __forceinline__ void store_one(const GramJob& g, int64_t row, int64_t col,
                                           uint32_t x) {
-    if (kMode == kTcModeMI) {
+    if (is_mi<kMode>()) {
         g.out_f[row * g.ld_out + col] = __uint_as_float(x);
     } else if (kMode == kTcModeCounts) {
         g.out_c[row * g.ld_out + col] = static_cast<int32_t>(x);
@@ -391,9 +400,12 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int lane_base = (warp & 3) * 32;             // TMEM lanes this warp may access
-    const int half = (warp - 2) >> 2;                  // which half of the tile's columns
-    MiVar* cv = sm.colvars(warp - 2);                  // this warp's column terms
+    constexpr int kNepi = epi_warps(kMode);
+    constexpr int kParts = kNepi / 4;                  // warps per TMEM lane quadrant
+    const int part = (warp - 2) >> 2;                  // which part of the tile's columns
+    MiVar* cv = sm.colvars(warp - 2, kNepi);           // this warp's column terms
     const float cscale = L.direct ? 262144.f : 1.f;    // 2^18: direct operands hold 2^-9
+    constexpr bool kFix = kMode == kTcModeMI;          // FP64 combine compiled in
     int acc = 0;
     uint32_t acc_phase = 0;
     int qslot = 0;
@@ -420,9 +432,11 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
         if (t < 0) break;
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
-        const MiParams& P = job.mp;
-        const int cols = job.bn >> 1;                  // columns of this warp
-        const int col_base = half * cols;
+        // copies in registers: the epilogue's stores could otherwise alias the
+        // job table and force these fields to be reloaded after every store
+        const MiParams P = job.mp;
+        const int cols = job.bn / kParts;              // columns of this warp
+        const int col_base = part * cols;
         const int64_t n_a = job.n_a, n_b = job.n_b;
         const bool sym = job.symmetric != 0;
         const int64_t ibase = static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m +
@@ -435,7 +449,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
         A.r1 = A.r0 = A.rchi = 0.f;
         A.h = 0.0;
         A.unused = 0.0;
-        if (kMode == kTcModeMI) {
+        if (is_mi<kMode>()) {
             // stage the per-variable terms of this warp's columns while the
             // accumulator is still being produced
             __syncwarp();
@@ -457,6 +471,68 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
         ptx::tc_fence_after();
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(lane_base) << 16) +
                                static_cast<uint32_t>(acc * kAccCols + col_base);
+        if constexpr (kMode == kTcModeMI32) {
+            // FP32 MI: chunks of 4 columns in one small loop body; the next
+            // chunk's accumulator columns load from TMEM during this chunk's math
+            const int64_t c_end64 = n_b - jstart < cols ? n_b - jstart : cols;
+            const int c_end = c_end64 <= 0 ? 0 : static_cast<int>((c_end64 + 3) & ~int64_t{3});
+            int c = 0;
+            if (sym && ibase > jstart)   // chunks entirely below the diagonal for all 32 rows
+                c = static_cast<int>(((ibase - jstart) / 4) * 4);
+            float* const out_f = job.out_f;
+            float* const out_t = job.out_t;
+            const int64_t ld_out = job.ld_out, ld_t = job.ld_t;
+            const bool vec_store = job.vec_store != 0;
+            uint32_t cur[4];
+            if (c < c_end) {
+                ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(c), cur);
+                ptx::tmem_wait_ld();
+            }
+#pragma unroll 1
+            for (; c < c_end; c += 4) {
+                uint32_t nxt[4];
+                const bool more = c + 4 < c_end;
+                if (more) ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(c + 4), nxt);
+                const int64_t j0 = jstart + c;
+                float v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t j = j0 + q;
+                    const int32_t n11 = __float2int_rn(__uint_as_float(cur[q]) * cscale);
+                    float mi = 0.f;
+                    if (row_ok && j < n_b && (!sym || j >= i)) {
+                        const MiVar B = cv[c + q];
+                        const MiCounts cc = mi_counts(n11, A.v, B.v, P);
+                        if (cc.det != 0)
+                            mi = fmaxf(mi_fp32(cc, static_cast<float>(cc.det), A, B, P), 0.f);
+                    }
+                    v[q] = mi;
+                }
+                if (row_ok) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int64_t j = j0 + q;
+                        if (sym && j < n_b && j > i) out_f[j * ld_out + i] = v[q];
+                        if (out_t != nullptr && j < n_b) out_t[j * ld_t + i] = v[q];
+                    }
+                    if (j0 + 4 <= n_b && (!sym || j0 >= i) && vec_store) {
+                        *reinterpret_cast<float4*>(out_f + i * ld_out + j0) =
+                            make_float4(v[0], v[1], v[2], v[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int64_t j = j0 + q;
+                            if (j < n_b && (!sym || j >= i)) out_f[i * ld_out + j] = v[q];
+                        }
+                    }
+                }
+                if (more) {
+                    ptx::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+                }
+            }
+        } else
 #pragma unroll 1
         for (int g = 0; g < cols; g += kGroup) {
             const int64_t j0 = jstart + g;
@@ -467,7 +543,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             uint32_t r[kGroup];
             ptx::tmem_ld_32x32b_x16(taddr + static_cast<uint32_t>(g), r);
             ptx::tmem_wait_ld();
-            if (kMode == kTcModeMI) {
+            if (is_mi<kMode>()) {
                 // pass 1: FP32 MI, or a mark for the FP64 combine
                 uint32_t need64 = 0;
 #pragma unroll
@@ -480,10 +556,10 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                         const MiCounts c = mi_counts(n11, A.v, B.v, P);
                         if (c.det != 0) {
                             const float fdet = static_cast<float>(c.det);
-                            bool small = P.fixup && mi_surely_small(fdet, A, B, P);
+                            bool small = kFix && P.fixup && mi_surely_small(fdet, A, B, P);
                             if (!small) {
                                 mi = fmaxf(mi_fp32(c, fdet, A, B, P), 0.f);
-                                small = P.fixup && mi < P.fixup_below;
+                                small = kFix && P.fixup && mi < P.fixup_below;
                             }
                             if (small) need64 |= 1u << q;
                         }
@@ -492,7 +568,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                                               : __float_as_uint(mi);
                 }
                 // pass 2: FP64 n log n combine, table reads issued four pairs at a time
-                if (__any_sync(0xffffffffu, need64 != 0)) {
+                if (kFix && __any_sync(0xffffffffu, need64 != 0)) {
 #pragma unroll
                     for (int q0 = 0; q0 < kGroup; q0 += 4) {
                         double tv[4][4];
@@ -536,7 +612,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                 }
             }
             // mirror into a separate buffer (panels of an out-of-core run)
-            if (kMode == kTcModeMI && job.out_t != nullptr && row_ok) {
+            if (is_mi<kMode>() && job.out_t != nullptr && row_ok) {
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q) {
                     const int64_t j = j0 + q;
@@ -547,7 +623,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             if (!row_ok) continue;
             const bool full = (j0 + kGroup <= n_b) && (!sym || j0 >= i);
             if (full && job.vec_store) {
-                if (kMode == kTcModeMI) {
+                if (is_mi<kMode>()) {
                     float4* dst = reinterpret_cast<float4*>(job.out_f + i * job.ld_out + j0);
 #pragma unroll
                     for (int q = 0; q < kGroup / 4; ++q)
@@ -613,7 +689,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
 }
 
 template <int kMode, bool kPair>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_of(kMode), 1)
 gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__ GramLaunch L) {
     extern __shared__ uint8_t smem_raw[];
     Smem<kPair> sm;
@@ -633,13 +709,13 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(sm.tfull(b), 1);
             // pair: one arrival per epilogue warp of both CTAs, on CTA 0
-            ptx::mbar_init(sm.tempty(b), kPair ? 2 * kEpiWarps : kEpiWarps * 32);
+            ptx::mbar_init(sm.tempty(b), kPair ? 2 * epi_warps(kMode) : epi_warps(kMode) * 32);
         }
         ptx::mbar_init(sm.drain(), 1);
         for (int q = 0; q < kQ; ++q) {
             ptx::mbar_init(sm.qfull(q), 1);
             // MMA thread + one lane per epilogue warp (pair: of both CTAs, on CTA 0)
-            ptx::mbar_init(sm.qempty(q), 1 + (kPair ? 2 : 1) * kEpiWarps);
+            ptx::mbar_init(sm.qempty(q), 1 + (kPair ? 2 : 1) * epi_warps(kMode));
         }
         *sm.abort_flag() = 0;
         ptx::fence_barrier_init();
@@ -701,6 +777,9 @@ cudaError_t set_smem_attrs() {
     e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI, kPair>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI32, kPair>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeCounts, kPair>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -714,7 +793,7 @@ cudaError_t launch_pair(const OperandMaps& maps, const GramLaunch& L, int grid,
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(threads_of(kMode), 1, 1);
     cfg.dynamicSmemBytes = Plan<true>::smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -737,11 +816,16 @@ cudaError_t gram_tc_prepare() {
     return set_smem_attrs<true>();
 }
 
+int gram_tc_epilogue_warps(int mode, int fixup) {
+    const int m = (mode == kTcModeMI && !fixup) ? kTcModeMI32 : mode;
+    return epi_warps(m);
+}
+
 int gram_tc_pair_clusters() {
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(2, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(threads_of(kTcModeMI32), 1, 1);
     cfg.dynamicSmemBytes = Plan<true>::smem_bytes;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -751,7 +835,7 @@ int gram_tc_pair_clusters() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, gram_tc_kernel<kTcModeMI, true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, gram_tc_kernel<kTcModeMI32, true>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -785,9 +869,12 @@ void gram_tiles(int job, int64_t n_a, int64_t n_b, int bn, bool symmetric, int g
 cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int grid,
                            cudaStream_t s) {
     if (L.num_tiles <= 0 || grid <= 0) return cudaSuccess;
+    // MI with the FP64 combine off runs the kernel without its code
+    const int mode = (L.mode == kTcModeMI && !L.fixup) ? kTcModeMI32 : L.mode;
     if (L.pair) {
         if (grid % 2 != 0 || L.direct) return cudaErrorInvalidValue;
-        switch (L.mode) {
+        switch (mode) {
+            case kTcModeMI32: return launch_pair<kTcModeMI32>(maps, L, grid, s);
             case kTcModeMI: return launch_pair<kTcModeMI>(maps, L, grid, s);
             case kTcModeCounts: return launch_pair<kTcModeCounts>(maps, L, grid, s);
             case kTcModeCountsAdd: return launch_pair<kTcModeCountsAdd>(maps, L, grid, s);
@@ -795,15 +882,18 @@ cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int gri
         }
     }
     constexpr size_t kSmem = Plan<false>::smem_bytes;
-    switch (L.mode) {
+    switch (mode) {
+        case kTcModeMI32:
+            gram_tc_kernel<kTcModeMI32, false><<<grid, threads_of(kTcModeMI32), kSmem, s>>>(maps, L);
+            break;
         case kTcModeMI:
-            gram_tc_kernel<kTcModeMI, false><<<grid, kThreads, kSmem, s>>>(maps, L);
+            gram_tc_kernel<kTcModeMI, false><<<grid, threads_of(kTcModeMI), kSmem, s>>>(maps, L);
             break;
         case kTcModeCounts:
-            gram_tc_kernel<kTcModeCounts, false><<<grid, kThreads, kSmem, s>>>(maps, L);
+            gram_tc_kernel<kTcModeCounts, false><<<grid, threads_of(kTcModeCounts), kSmem, s>>>(maps, L);
             break;
         case kTcModeCountsAdd:
-            gram_tc_kernel<kTcModeCountsAdd, false><<<grid, kThreads, kSmem, s>>>(maps, L);
+            gram_tc_kernel<kTcModeCountsAdd, false><<<grid, threads_of(kTcModeCountsAdd), kSmem, s>>>(maps, L);
             break;
         default:
             return cudaErrorInvalidValue;

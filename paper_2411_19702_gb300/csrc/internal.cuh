@@ -179,6 +179,9 @@ struct GramLaunch {
     const unsigned int* panel_target;
     unsigned int* host_flags;
     int panel_blocks;
+    // MI mode: 1 if any job has the FP64 combine on (then the kernel that
+    // contains it is launched; else the one without it)
+    int fixup;
 };
 
 // TMA descriptors of a K-block-major operand buffer of total_rows rows of 128
@@ -205,6 +208,9 @@ size_t gram_tc_smem_bytes();
 cudaError_t gram_tc_prepare();   // set the kernels' shared-memory attribute (current device)
 // CTA pairs (clusters of 2) of the pair kernel that fit on the device at once.
 int gram_tc_pair_clusters();
+// Epilogue warps per CTA of the kernel a launch of this mode runs (each
+// signals a finished tile once in panel-completion counting).
+int gram_tc_epilogue_warps(int mode, int fixup);
 
 // Set the text gbmi_last_error_string() returns on this host thread.
 void set_last_error(const char* msg);
