@@ -276,6 +276,45 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------- library comparator
+def measure_library_plain(X, m, n, fused_out, reps=5):
+    """The same two steps on library calls, for context: the transposed FP8 operand by torch
+    ops, N11 by cuBLASLt's FP8 GEMM (torch._scaled_mm, FP32 output), then this library's
+    elementwise MI kernel on the counts."""
+    import torch
+
+    from paper_2411_19702_gb300 import gbmi
+    dev = X.device
+    try:
+        one = torch.ones((), device=dev)
+
+        def step():
+            Xt = X.t().contiguous().to(torch.float8_e4m3fn)          # pack: transpose + FP8
+            N = torch._scaled_mm(Xt, Xt.t(), scale_a=one, scale_b=one, out_dtype=torch.float32)
+            N11 = N.to(torch.int32)
+            v = torch.diagonal(N11).contiguous()
+            return gbmi.mi_from_counts(N11, v, v, m)
+        out = step()
+        gbmi.sync()
+        rows = torch.arange(0, n, 97, device=dev)
+        same = bool(torch.equal(out[rows], fused_out[rows]))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = step()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        del out
+        torch.cuda.empty_cache()
+        return {"ms_per_step": ms, "value": n * (n - 1) / 2 / (ms * 1e-3),
+                "steps": "torch transpose + FP8 cast, cuBLASLt FP8 GEMM (FP32 out), int32 cast, "
+                         "elementwise MI kernel (both triangles)",
+                "sampled_rows_bit_identical_to_fused": same}
+    except Exception as e:  # a torch build without FP8 GEMM on this device
+        return {"unavailable": str(e).splitlines()[0][:200]}
+
+
 # --------------------------------------------------------------- batching
 def batch_shapes(k=512, seed=4):
     """Dataset shapes and column densities of the batching workload."""
@@ -709,6 +748,12 @@ def run_ours(args):
                    "share": v["ms"] / step_total if step_total > 0 else None}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
+    library = None
+    if rank == 0 and not args.skip_library:
+        step("fused")
+        gbmi.sync()
+        library = measure_library_plain(X, m, n, out)
+
     # end to end through the host-buffer C-ABI call (pinned buffers)
     e2e = None
     if not args.skip_e2e:
@@ -773,6 +818,7 @@ def run_ours(args):
                                                  f"x {clk_mhz:.0f} MHz (median SM clock)",
                                   "words_per_pair": words}},
         "fused_over_plain": plain_ms / fused_ms,
+        "library_plain": library,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "gram_tc_fused_mi",
@@ -814,6 +860,7 @@ def main():
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-ooc", action="store_true")
     ap.add_argument("--skip-sparse", action="store_true")
+    ap.add_argument("--skip-library", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
