@@ -429,12 +429,19 @@ gbmi_status pipeline_resources(DeviceCtx& c, int events, int panels) {
 
 // Host buffers, fused tensor-core path, pipelined:
 //   X (and Y) go up in row chunks on a copy stream, each chunk packed as soon
-//   as it lands (the pack hides under the upload);
-//   one Gram launch runs the tiles in panel-major order (row panels of
+//   as it lands;
+//   the Gram runs over the samples in kGramChunks chunks: each of the first
+//   ones accumulates exact int32 counts in HBM (counts / counts-add launches)
+//   while later chunks are still uploading, and the last one runs the fused
+//   MI epilogue with those counts added to its accumulator;
+//   that last launch takes its tiles in panel-major order (row panels of
 //   panel_blocks tile rows), and the epilogue flags each finished panel in
 //   mapped host memory; the host copies a panel's rows down as soon as it and
 //   every earlier panel are flagged (rows of panel p are written only by
 //   tiles of panels <= p), so the download overlaps the rest of the Gram.
+constexpr int kUploadChunks = 8;
+constexpr int kGramChunks = 4;
+
 gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int64_t m,
                            int64_t n1, int64_t n2, float* out, bool sym) {
     TcLayout L;
@@ -454,6 +461,16 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
         GBMI_TRY(ensure(c.vb, static_cast<size_t>(n2) * 4, "column counts"));
     }
     GBMI_TRY(ensure(c.outs, ob, "output staging"));
+    MiParams mp;
+    GBMI_TRY(rt::mi_params(c, m, &mp));
+
+    // upload chunks (rows, multiples of 128) and Gram chunks (groups of them)
+    const int64_t R = std::max<int64_t>(kTcBK * 64, round_up((m + kUploadChunks - 1) / kUploadChunks,
+                                                              kTcBK));
+    const int uchunks = static_cast<int>((m + R - 1) / R);
+    // the FP64-combine kernel variant has no prefix input: one Gram launch then
+    const int gchunks = mp.fixup ? 1 : std::min(kGramChunks, uchunks);
+    if (gchunks > 1) GBMI_TRY(ensure(c.counts, ob, "count matrix"));
 
     // tiles in panel-major order
     const int bn_single = rt::choose_bn(m, n1, n2, sym);
@@ -464,12 +481,10 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
     const int64_t pblocks = std::max<int64_t>(1, (TI + 7) / 8);   // about eight panels
     const int64_t panels = (TI + pblocks - 1) / pblocks;
     const int group = std::max(1, g_opt.group_cols);
-    std::vector<GramTile> tiles;
-    std::vector<unsigned int> target(static_cast<size_t>(panels), 0);
-    MiParams mp;
-    GBMI_TRY(rt::mi_params(c, m, &mp));
     const unsigned int epi = static_cast<unsigned int>(
         gram_tc_epilogue_warps(kTcModeMI, mp.fixup) * (pair ? 2 : 1));
+    std::vector<GramTile> tiles;
+    std::vector<unsigned int> target(static_cast<size_t>(panels), 0);
     for (int64_t p = 0; p < panels; ++p) {
         const int64_t I0 = p * pblocks, I1 = std::min(TI, I0 + pblocks);
         for (int64_t g0 = 0; g0 < TJ; g0 += group)
@@ -481,9 +496,7 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
                 }
     }
     if (tiles.size() > 0x7FFFFFFFu) return fail(GBMI_ERR_ARG, "too many tiles");
-    const int64_t R = std::max<int64_t>(kTcBK * 64, round_up((m + 7) / 8, kTcBK));   // chunk rows
-    const int chunks = static_cast<int>((m + R - 1) / R) * (sym ? 1 : 2);
-    GBMI_TRY(pipeline_resources(c, chunks, static_cast<int>(panels)));
+    GBMI_TRY(pipeline_resources(c, uchunks * (sym ? 1 : 2), static_cast<int>(panels)));
     GBMI_TRY(ensure(c.tiles, tiles.size() * sizeof(GramTile), "tile list"));
     c.tl_na = -1;   // the single-call tile cache no longer holds this buffer's contents
     cudaStream_t cs = c.copy_stream;
@@ -499,72 +512,97 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
     GBMI_CUDA(cudaMemsetAsync(counters, 0, static_cast<size_t>(panels) * 4, g_stream),
               "panel counters");
 
-    // upload in chunks, pack each chunk as it lands
+    uint8_t* P = static_cast<uint8_t*>(c.P.p);
     int ev = 0;
-    auto upload_pack = [&](const uint8_t* src, uint8_t* stage, int64_t n, uint8_t* P,
+    // upload row chunk u of one operand and pack it as soon as it lands
+    auto upload_pack = [&](int u, const uint8_t* src, uint8_t* stage, int64_t n, uint8_t* Pop,
                            int64_t rows_p, int32_t* v) -> gbmi_status {
-        GBMI_LAUNCH(launch_zero_u32(v, n, g_stream), "zero");
-        for (int64_t r0 = 0; r0 < m; r0 += R) {
-            const int64_t rows = std::min(R, m - r0);
-            GBMI_CUDA(cudaMemcpyAsync(stage + r0 * n, src + r0 * n, static_cast<size_t>(rows) * n,
-                                      cudaMemcpyHostToDevice, cs),
-                      "copy in");
-            GBMI_CUDA(cudaEventRecord(c.events[ev], cs), "event");
-            GBMI_CUDA(cudaStreamWaitEvent(g_stream, c.events[ev], 0), "wait chunk");
-            ++ev;
-            PackJob j;
-            std::memset(&j, 0, sizeof(j));
-            j.X = stage + r0 * n;
-            j.m = rows;
-            j.n = n;
-            j.ldx = n;
-            j.P = P + (r0 / kTcBK) * rows_p * kTcBK;
-            j.v = v;
-            j.rows_p = rows_p;
-            j.ldp = pack_ld(rows);
-            GBMI_LAUNCH(launch_pack(j, g_stream), "pack");
-        }
+        const int64_t r0 = u * R, rows = std::min(R, m - r0);
+        GBMI_CUDA(cudaMemcpyAsync(stage + r0 * n, src + r0 * n, static_cast<size_t>(rows) * n,
+                                  cudaMemcpyHostToDevice, cs),
+                  "copy in");
+        GBMI_CUDA(cudaEventRecord(c.events[ev], cs), "event");
+        GBMI_CUDA(cudaStreamWaitEvent(g_stream, c.events[ev], 0), "wait chunk");
+        ++ev;
+        PackJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.X = stage + r0 * n;
+        j.m = rows;
+        j.n = n;
+        j.ldx = n;
+        j.P = Pop + (r0 / kTcBK) * rows_p * kTcBK;
+        j.v = v;
+        j.rows_p = rows_p;
+        j.ldp = pack_ld(rows);
+        GBMI_LAUNCH(launch_pack(j, g_stream), "pack");
         return GBMI_OK;
     };
-    uint8_t* P = static_cast<uint8_t*>(c.P.p);
-    GBMI_TRY(upload_pack(X, static_cast<uint8_t*>(c.Xs.p), n1, P, L.rows_a,
-                         static_cast<int32_t*>(c.va.p)));
-    if (!sym)
-        GBMI_TRY(upload_pack(Y, static_cast<uint8_t*>(c.Ys.p), n2, P + L.kb * L.rows_a * kTcBK,
-                             L.rows_b, static_cast<int32_t*>(c.vb.p)));
-
-    const MiVar *va = nullptr, *vb = nullptr;
-    GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.va.p), n1, mp, c.ha, &va));
-    if (sym)
-        vb = va;
-    else
-        GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.vb.p), n2, mp, c.hb, &vb));
+    GBMI_LAUNCH(launch_zero_u32(c.va.p, n1, g_stream), "zero");
+    if (!sym) GBMI_LAUNCH(launch_zero_u32(c.vb.p, n2, g_stream), "zero");
 
     OperandMaps maps;
     if (!make_operand_maps(&maps, P, L.total_rows))
         return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    GBMI_TRY(ensure(c.sched, 256, "tile counter"));
     GramLaunch G;
     std::memset(&G, 0, sizeof(G));
-    G.job0 = tc_job(L, m, n1, n2, sym, bn, va, vb, mp, static_cast<float*>(c.outs.p), nullptr);
+    G.job0 = tc_job(L, m, n1, n2, sym, bn, nullptr, nullptr, mp, nullptr, nullptr);
     G.job0.bn = bn;
     G.tiles = static_cast<const GramTile*>(c.tiles.p);
     G.num_tiles = static_cast<int>(tiles.size());
-    G.mode = kTcModeMI;
     G.err = static_cast<unsigned int*>(c.err.p);
     G.timeout_ns = g_opt.timeout_ns;
     G.debug_flags = g_opt.debug_flags;
     G.pair = pair ? 1 : 0;
     G.fixup = mp.fixup;
-    GBMI_TRY(ensure(c.sched, 256, "tile counter"));
     G.counter = static_cast<unsigned int*>(c.sched.p);
-    G.panel_done = counters;
-    G.panel_target = targets;
-    G.host_flags = c.dflags;
-    G.panel_blocks = static_cast<int>(pblocks);
     const int grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, G.num_tiles))
                           : rt::grid_for(c, G.num_tiles);
-    GBMI_CUDA(cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
-    GBMI_LAUNCH(launch_gram_tc(maps, G, grid, g_stream), "gram_tc_fused_mi");
+    int32_t* const counts = static_cast<int32_t*>(c.counts.p);
+    for (int g = 0; g < gchunks; ++g) {
+        const int u0 = g * uchunks / gchunks, u1 = (g + 1) * uchunks / gchunks;
+        for (int u = u0; u < u1; ++u) {
+            GBMI_TRY(upload_pack(u, X, static_cast<uint8_t*>(c.Xs.p), n1, P, L.rows_a,
+                                 static_cast<int32_t*>(c.va.p)));
+            if (!sym)
+                GBMI_TRY(upload_pack(u, Y, static_cast<uint8_t*>(c.Ys.p), n2,
+                                     P + L.kb * L.rows_a * kTcBK, L.rows_b,
+                                     static_cast<int32_t*>(c.vb.p)));
+        }
+        const int64_t kb0 = (u0 * R) / kTcBK;
+        const int64_t kb1 = g + 1 < gchunks ? (u1 * R) / kTcBK : L.kb;
+        G.job0.k_begin = static_cast<int32_t>(kb0);
+        G.job0.k_blocks = static_cast<int32_t>(kb1 - kb0);
+        if (g + 1 < gchunks) {   // counts of this sample chunk, kept in HBM
+            G.mode = g == 0 ? kTcModeCounts : kTcModeCountsAdd;
+            G.job0.out_f = nullptr;
+            G.job0.out_c = counts;
+            GBMI_CUDA(cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), g_stream),
+                      "tile counter");
+            GBMI_LAUNCH(launch_gram_tc(maps, G, grid, g_stream),
+                        g == 0 ? "gram_tc_counts" : "gram_tc_counts_add");
+            continue;
+        }
+        // last chunk: the fused MI epilogue, earlier chunks' counts added
+        const MiVar *va = nullptr, *vb = nullptr;
+        GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.va.p), n1, mp, c.ha, &va));
+        if (sym)
+            vb = va;
+        else
+            GBMI_TRY(mi_vars(static_cast<const int32_t*>(c.vb.p), n2, mp, c.hb, &vb));
+        G.mode = kTcModeMI;
+        G.job0.va = va;
+        G.job0.vb = vb;
+        G.job0.out_f = static_cast<float*>(c.outs.p);
+        G.job0.out_c = gchunks > 1 ? counts : nullptr;
+        G.job0.vec_store = (n2 % 4 == 0) ? 1 : 0;
+        G.panel_done = counters;
+        G.panel_target = targets;
+        G.host_flags = c.dflags;
+        G.panel_blocks = static_cast<int>(pblocks);
+        GBMI_CUDA(cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
+        GBMI_LAUNCH(launch_gram_tc(maps, G, grid, g_stream), "gram_tc_fused_mi");
+    }
 
     // download each panel once it and every earlier panel are complete; if
     // the launch ends first (or fails), the rest follows it on the stream

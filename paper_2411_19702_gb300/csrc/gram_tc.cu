@@ -483,6 +483,8 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             float* const out_t = job.out_t;
             const int64_t ld_out = job.ld_out, ld_t = job.ld_t;
             const bool vec_store = job.vec_store != 0;
+            // counts of earlier sample chunks (or null): n11 = prefix + this launch's
+            const int32_t* const prefix = job.out_c;
             uint32_t cur[4];
             if (c < c_end) {
                 ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(c), cur);
@@ -498,9 +500,10 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int64_t j = j0 + q;
-                    const int32_t n11 = __float2int_rn(__uint_as_float(cur[q]) * cscale);
+                    int32_t n11 = __float2int_rn(__uint_as_float(cur[q]) * cscale);
                     float mi = 0.f;
                     if (row_ok && j < n_b && (!sym || j >= i)) {
+                        if (prefix != nullptr) n11 += prefix[i * ld_out + j];
                         const MiVar B = cv[c + q];
                         const MiCounts cc = mi_counts(n11, A.v, B.v, P);
                         if (cc.det != 0)
