@@ -74,3 +74,19 @@ def test_repeated_calls_reuse_the_pipeline():
     want = gbmi.mi_all_pairs(torch.from_numpy(X).cuda(), path="fused").cpu()
     gbmi.sync()
     assert torch.equal(outs[0], want)
+
+
+def test_host_call_with_fp64_combine_runs_one_gram_chunk():
+    X = _data(70_001, 600, 4)
+    gbmi.set_option(gbmi.OPT_FIXUP, 1)
+    try:
+        want = gbmi.mi_all_pairs(torch.from_numpy(X).cuda(), path="fused").cpu()
+        gbmi.sync()
+        out = torch.empty((600, 600), dtype=torch.float32).pin_memory()
+        gbmi.mi_all_pairs_host(torch.from_numpy(X).pin_memory(), out)
+    finally:
+        gbmi.set_option(gbmi.OPT_FIXUP, 0)
+    assert torch.equal(out, want)
+    default = torch.empty((600, 600), dtype=torch.float32)
+    gbmi.mi_all_pairs_host(torch.from_numpy(X), default)          # four Gram chunks
+    assert float((default - out).abs().max()) <= 1e-6
