@@ -59,12 +59,16 @@ typedef enum {
     GBMI_PATH_POPCOUNT = 3   /* bit-packed AND + popcount Gram (exactness cross-check)      */
 } gbmi_path;
 
-/* Options for gbmi_set_option. */
+/* Options for gbmi_set_option.  Their defaults can also be set in the
+ * environment when the library loads: GBMI_FIXUP, GBMI_TILE_N, GBMI_PAIR,
+ * GBMI_DIRECT, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS (out-of-range
+ * values are ignored).  GBMI_LOG=1 also writes every error text to stderr. */
 typedef enum {
     GBMI_OPT_FIXUP = 1,          /* 1: FP64 n*log2(n) combine for pairs whose FP32 MI < 1e-4 (default 0) */
     GBMI_OPT_TIMEOUT_NS = 2,     /* bound of every device-side wait, ns (default 2e9)            */
     GBMI_OPT_DEBUG_FLAGS = 3,    /* test hooks; 1 = the fused kernel's loader issues no copies,
-                                    so its consumer's bounded wait must run out (default 0)      */
+                                    so its consumer's bounded wait must run out; 2 = every new
+                                    workspace allocation fails with GBMI_ERR_OOM (default 0)     */
     GBMI_OPT_GROUP_COLS = 4,     /* tile-order group width in 256-column blocks (default 8)      */
     GBMI_OPT_MAX_CTAS = 5,       /* cap on persistent CTAs, 0 = one per SM (default 0)           */
     GBMI_OPT_PROFILE = 6,        /* 1: time every kernel launch with CUDA events (default 0)     */
@@ -315,6 +319,15 @@ gbmi_status gbmi_server_submit(gbmi_server* srv, int64_t a, int64_t b, int64_t* 
 gbmi_status gbmi_server_wait(gbmi_server* srv, int64_t ticket, int64_t timeout_ms,
                              const float** out, double* latency_ms);
 gbmi_status gbmi_server_release(gbmi_server* srv, int64_t ticket);
+/* Cancel a request that is still queued (GBMI_ERR_ARG if it is running or
+ * done): gbmi_server_wait then returns GBMI_ERR_ARG for it, and it must still
+ * be released. */
+gbmi_status gbmi_server_cancel(gbmi_server* srv, int64_t ticket);
+/* Requests queued and running, datasets registered, and arena bytes in use
+ * (packed datasets, per-variable terms, unreleased outputs); any pointer may
+ * be NULL. */
+gbmi_status gbmi_server_state(gbmi_server* srv, int64_t* queued, int64_t* running,
+                              int64_t* datasets, int64_t* bytes_in_use);
 gbmi_status gbmi_server_stats(gbmi_server* srv, double* stats);
 gbmi_status gbmi_server_destroy(gbmi_server* srv);
 

@@ -1,4 +1,6 @@
 // Host runtime shared by the C-ABI translation units (see runtime.h).
+#include <cstdio>
+#include <cstdlib>
 #include "runtime.h"
 
 #include <algorithm>
@@ -17,6 +19,48 @@ namespace rt {
 
 std::recursive_mutex g_mu;
 Options g_opt;
+
+namespace {
+// GBMI_LOG=1: every error text is also written to stderr.
+bool log_errors() {
+    static const bool on = [] {
+        const char* e = std::getenv("GBMI_LOG");
+        return e != nullptr && std::atoi(e) > 0;
+    }();
+    return on;
+}
+
+// Option defaults from the environment (GBMI_FIXUP, GBMI_TILE_N, GBMI_PAIR,
+// GBMI_DIRECT, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS), read once
+// when the library loads; values out of range are ignored.
+struct EnvOptions {
+    EnvOptions() {
+        auto num = [](const char* name, long long lo, long long hi, long long* out) {
+            const char* e = std::getenv(name);
+            if (e == nullptr || *e == '\0') return false;
+            char* end = nullptr;
+            const long long v = std::strtoll(e, &end, 10);
+            if (end == e || *end != '\0' || v < lo || v > hi) {
+                if (log_errors()) std::fprintf(stderr, "gbmi: ignoring %s=%s\n", name, e);
+                return false;
+            }
+            *out = v;
+            return true;
+        };
+        long long v = 0;
+        if (num("GBMI_FIXUP", 0, 1, &v)) g_opt.fixup = static_cast<int>(v);
+        if (num("GBMI_TILE_N", 0, 256, &v) && (v == 0 || v == 64 || v == 128 || v == 256))
+            g_opt.tile_n = static_cast<int>(v);
+        if (num("GBMI_PAIR", 0, 2, &v)) g_opt.pair = static_cast<int>(v);
+        if (num("GBMI_DIRECT", 0, 1, &v)) g_opt.direct = static_cast<int>(v);
+        if (num("GBMI_TIMEOUT_NS", 1000, 600000000000LL, &v))
+            g_opt.timeout_ns = static_cast<uint64_t>(v);
+        if (num("GBMI_GROUP_COLS", 1, 1 << 20, &v)) g_opt.group_cols = static_cast<int>(v);
+        if (num("GBMI_MAX_CTAS", 0, 1 << 20, &v)) g_opt.max_ctas = static_cast<int>(v);
+    }
+};
+EnvOptions g_env_options;
+}  // namespace
 cudaStream_t g_stream = nullptr;
 std::atomic<uint64_t> g_launches{0};
 
@@ -71,17 +115,21 @@ std::pair<int, int> bucket(int64_t m, int64_t n) {
 
 gbmi_status fail(gbmi_status s, const std::string& msg) {
     t_last_error = msg;
+    if (log_errors()) std::fprintf(stderr, "gbmi: %s\n", msg.c_str());
     return s;
 }
 
 gbmi_status cuda_fail(cudaError_t e, const char* what) {
-    t_last_error = std::string(what) + ": " + cudaGetErrorString(e);
-    return e == cudaErrorMemoryAllocation ? GBMI_ERR_OOM : GBMI_ERR_CUDA;
+    return fail(e == cudaErrorMemoryAllocation ? GBMI_ERR_OOM : GBMI_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 gbmi_status ensure(DevBuf& b, size_t bytes, const char* what) {
     if (bytes == 0) bytes = 256;
     if (b.cap >= bytes) return GBMI_OK;
+    if (g_opt.debug_flags & 2)   // test hook: every new workspace allocation fails
+        return fail(GBMI_ERR_OOM, std::string("device allocation of ") + std::to_string(bytes) +
+                                      " bytes for " + what + " refused (injected failure)");
     if (b.p != nullptr) {
         cudaError_t e = cudaFree(b.p);   // implicitly waits for the device
         b.p = nullptr;
@@ -92,9 +140,8 @@ gbmi_status ensure(DevBuf& b, size_t bytes, const char* what) {
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
-        t_last_error = std::string("device allocation of ") + std::to_string(bytes) +
-                       " bytes for " + what + " failed: " + cudaGetErrorString(e);
-        return GBMI_ERR_OOM;
+        return fail(GBMI_ERR_OOM, std::string("device allocation of ") + std::to_string(bytes) +
+                                      " bytes for " + what + " failed: " + cudaGetErrorString(e));
     }
     b.cap = bytes;
     return GBMI_OK;

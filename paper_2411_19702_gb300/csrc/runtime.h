@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -100,10 +101,14 @@ int grid_for(const DeviceCtx& c, int64_t tiles);
         if (e_ != cudaSuccess) return ::gbmi::rt::cuda_fail(e_, (what)); \
     } while (0)
 
+// One kernel launch: an NVTX range around the enqueue (visible to profilers
+// that collect NVTX), the optional event profiler, the launch counter.
 #define GBMI_LAUNCH_ON(stream, call, what)                            \
     do {                                                              \
+        nvtxRangePushA(what);                                         \
         cudaEvent_t ev0_ = ::gbmi::rt::prof_begin(stream);            \
         cudaError_t e_ = (call);                                      \
+        nvtxRangePop();                                               \
         if (e_ != cudaSuccess) return ::gbmi::rt::cuda_fail(e_, (what)); \
         ::gbmi::rt::prof_end((what), ev0_, stream);                   \
         ::gbmi::rt::g_launches.fetch_add(1, std::memory_order_relaxed); \

@@ -78,6 +78,7 @@ class Arena {
         }
     }
     size_t size() const { return size_; }
+    size_t used() const { return used_; }
 
    private:
     std::map<int64_t, size_t> free_;
@@ -99,7 +100,7 @@ struct Request {
     int64_t n_a = 0, n_b = 0, m = 0;
     int64_t off_out = -1;
     size_t bytes_out = 0;
-    int state = 0;                    // 0 queued, 1 running, 2 done, 3 failed
+    int state = 0;                    // 0 queued, 1 running, 2 done, 3 failed or cancelled
     gbmi_status err = GBMI_OK;
     Clock::time_point t_submit, t_done;
     int64_t pairs = 0;
@@ -626,9 +627,50 @@ gbmi_status gbmi_server_wait(gbmi_server* S, int64_t ticket, int64_t timeout_ms,
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return rt::fail(GBMI_ERR_ARG, "unknown ticket");
     const Request& r = it->second;
-    if (r.state == 3) return rt::fail(r.err, "request failed on the device");
+    if (r.state == 3)
+        return rt::fail(r.err, r.err == GBMI_ERR_ARG ? "request was cancelled (or the server closed)"
+                                                     : "request failed on the device");
     if (out) *out = reinterpret_cast<const float*>(at(S, r.off_out));
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+    return GBMI_OK;
+}
+
+gbmi_status gbmi_server_cancel(gbmi_server* S, int64_t ticket) {
+    if (S == nullptr) return rt::fail(GBMI_ERR_ARG, "null server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return rt::fail(GBMI_ERR_ARG, "unknown ticket");
+    Request& r = it->second;
+    if (r.state != 0) return rt::fail(GBMI_ERR_ARG, "request is not queued (running or done)");
+    for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+        if (*q == ticket) {
+            S->queue.erase(q);
+            break;
+        }
+    r.state = 3;
+    r.err = GBMI_ERR_ARG;
+    r.t_done = Clock::now();
+    for (int64_t id : {r.a, r.b}) {
+        if (id < 0) continue;
+        S->datasets[id].users -= 1;
+        drop_dataset_if_done(S, id);
+    }
+    lk.unlock();
+    S->cv_done.notify_all();
+    return GBMI_OK;
+}
+
+gbmi_status gbmi_server_state(gbmi_server* S, int64_t* queued, int64_t* running,
+                              int64_t* datasets, int64_t* bytes_in_use) {
+    if (S == nullptr) return rt::fail(GBMI_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    int64_t run = 0;
+    for (const Slot& sl : S->slots)
+        if (sl.busy) run += static_cast<int64_t>(sl.tickets.size());
+    if (queued) *queued = static_cast<int64_t>(S->queue.size());
+    if (running) *running = run;
+    if (datasets) *datasets = static_cast<int64_t>(S->datasets.size());
+    if (bytes_in_use) *bytes_in_use = static_cast<int64_t>(S->arena.used());
     return GBMI_OK;
 }
 

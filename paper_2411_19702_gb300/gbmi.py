@@ -94,6 +94,8 @@ def load(path: str | None = None):
             "gbmi_server_wait": [vp, i64, i64, vp, vp],
             "gbmi_server_release": [vp, i64],
             "gbmi_server_stats": [vp, vp],
+            "gbmi_server_cancel": [vp, i64],
+            "gbmi_server_state": [vp, vp, vp, vp, vp],
             "gbmi_server_destroy": [vp],
         }
         for name, args in sig.items():
@@ -622,6 +624,17 @@ class Server:
     def release(self, ticket: int):
         _check(load().gbmi_server_release(self._srv, int(ticket)))
         self._tshape.pop(ticket, None)
+
+    def cancel(self, ticket: int):
+        """Cancel a still-queued request (raises if it is running or done)."""
+        _check(load().gbmi_server_cancel(self._srv, int(ticket)))
+
+    def state(self) -> dict:
+        q, r, d, b = (ctypes.c_int64() for _ in range(4))
+        _check(load().gbmi_server_state(self._srv, ctypes.byref(q), ctypes.byref(r),
+                                        ctypes.byref(d), ctypes.byref(b)))
+        return {"queued": q.value, "running": r.value, "datasets": d.value,
+                "bytes_in_use": b.value}
 
     def stats(self) -> dict:
         st = (ctypes.c_double * 8)()

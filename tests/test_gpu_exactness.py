@@ -27,7 +27,8 @@ def _reset_options():
     gbmi.set_option(gbmi.OPT_TIMEOUT_NS, 2_000_000_000)
 
 
-@pytest.mark.parametrize("m", [1 << 10, 1 << 14, (1 << 20) + 3, 1 << 24])
+@pytest.mark.parametrize("m", [1 << 10, 1 << 14, (1 << 20) + 3, (1 << 24) - 1, 1 << 24,
+                               (1 << 24) + 1])
 def test_all_ones_counts_reach_m(m):
     n = 8
     X = torch.ones((m, n), dtype=torch.uint8, device="cuda")

@@ -23,8 +23,8 @@ pytestmark = pytest.mark.gpu
 
 MI_TOL = 1e-6
 PATHS = ["fused", "plain", "popcount"]
-SHAPES = [(1000, 200), (1, 1), (1, 5), (37, 1), (129, 127), (300, 257), (1031, 300),
-          (2000, 520)]
+SHAPES = [(1000, 200), (1, 1), (1, 5), (37, 1), (500, 2), (129, 127), (700, 128), (700, 129),
+          (300, 257), (1031, 300), (2000, 520)]
 
 
 def _data(m, n, seed, lo=0.02, hi=0.5):
@@ -241,3 +241,36 @@ def test_argument_errors():
     # the fused path refuses m > 2^24 (checked before touching memory)
     assert lib.gbmi_mi_all_pairs_path(big.data_ptr(), (1 << 24) + 1, 4, out.data_ptr(),
                                       gbmi.PATH_FUSED) == gbmi.ERR_ARG
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("m,n", [(1000, 200), (129, 127), (3000, 1100), (777, 33)])
+def test_every_output_element_is_written(path, m, n):
+    """The output starts as NaN; a tile or a mirror store that is skipped shows up."""
+    X = torch.from_numpy(_data(m, n, 31)).cuda()
+    out = torch.full((n, n), float("nan"), dtype=torch.float32, device="cuda")
+    gbmi.mi_all_pairs(X, out=out, path=path)
+    gbmi.sync()
+    assert not torch.isnan(out).any()
+    Y = torch.from_numpy(_data(m, 45, 32)).cuda()
+    outc = torch.full((n, 45), float("nan"), dtype=torch.float32, device="cuda")
+    gbmi.mi_cross(X, Y, out=outc, path=path)
+    gbmi.sync()
+    assert not torch.isnan(outc).any()
+
+
+def test_injected_allocation_failure_is_reported_and_recovers():
+    X = torch.from_numpy(_data(2000, 300, 33)).cuda()
+    gbmi.shutdown()                               # workspace released: the next call allocates
+    gbmi.set_option(gbmi.OPT_DEBUG_FLAGS, 2)
+    try:
+        with pytest.raises(gbmi.GbmiError) as e:
+            gbmi.mi_all_pairs(X, path="fused")
+        assert e.value.status == gbmi.ERR_OOM
+        assert "injected" in gbmi.last_error()
+    finally:
+        gbmi.set_option(gbmi.OPT_DEBUG_FLAGS, 0)
+    got = gbmi.mi_all_pairs(X, path="fused")
+    gbmi.sync()
+    want, _ = oracle.mi_matrix(X.cpu().numpy())
+    assert np.max(np.abs(got.cpu().numpy().astype(np.float64) - want)) <= MI_TOL

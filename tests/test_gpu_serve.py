@@ -155,3 +155,31 @@ def test_requests_on_cta_pairs_match_single_calls():
                     srv.release(t)
         finally:
             gbmi.set_option(gbmi.OPT_PAIR, 1)
+
+
+def test_cancel_queued_request_and_state():
+    X = _rand(5000, 1000, 90)
+    want = _alone(X, None)
+    out_bytes = 1000 * 1000 * 4
+    budget = 5120 * 1024 + 1000 * 32 + out_bytes + (3 << 20)   # one output at a time
+    with gbmi.Server(budget, max_batch=4) as srv:
+        ds = srv.add_dataset(X)
+        tickets = [srv.submit(ds) for _ in range(4)]
+        st = srv.state()
+        assert st["datasets"] == 1 and st["queued"] + st["running"] >= 3
+        srv.cancel(tickets[3])                   # outputs are held: it cannot have started
+        with pytest.raises(gbmi.GbmiError) as e:
+            srv.wait(tickets[3], timeout_ms=1000)
+        assert e.value.status == gbmi.ERR_ARG
+        for t in tickets[:3]:
+            got, _ = srv.wait(t, timeout_ms=60_000)
+            assert torch.equal(got, want)
+            with pytest.raises(gbmi.GbmiError):
+                srv.cancel(t)                    # done: not cancellable
+            srv.release(t)
+        srv.release(tickets[3])
+        st = srv.state()
+        assert st["queued"] == 0 and st["running"] == 0
+        assert st["bytes_in_use"] > 0            # the dataset stays resident until removed
+        srv.remove_dataset(ds)
+        assert srv.state()["datasets"] == 0

@@ -104,3 +104,22 @@ def test_csr_argument_errors_need_no_gpu():
     assert lib.gbmi_mi_all_pairs_csr(16, 16, 10, 4, 41, 16) == gbmi.ERR_ARG   # nnz > m * n
     assert lib.gbmi_counts_all_pairs_csr(16, 16, 0, 4, 0, 16) == gbmi.ERR_ARG  # m = 0
     assert lib.gbmi_counts_all_pairs_csr(16, 16, 10, 4, 3, None) == gbmi.ERR_ARG
+
+
+def test_environment_sets_option_defaults_and_logging():
+    import os
+    import subprocess
+    import sys
+    code = ("from paper_2411_19702_gb300 import gbmi; lib = gbmi.load(); "
+            "print(lib.gbmi_tile_n(100000, 10000)); "
+            "lib.gbmi_mi_all_pairs_to_host(None, 10, 4, None, 0)")
+    env = dict(os.environ, GBMI_TILE_N="64", GBMI_LOG="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))), timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "64"
+    assert "gbmi: null pointer" in r.stderr
+    env = dict(os.environ, GBMI_TILE_N="100")          # not a tile width: ignored
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))), timeout=120)
+    assert r.stdout.strip() != "100" and r.returncode == 0
