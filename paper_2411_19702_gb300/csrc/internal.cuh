@@ -16,7 +16,8 @@ namespace gbmi {
 //    one 128-byte row per variable (FP8 E4M3 0x00 / 0x38 = 1.0 per sample):
 //    byte (variable j, sample r) is at P[((r / 128) * rows_p + j) * 128 + r % 128].
 //    rows_p = n rounded up to 256, k_blocks = m rounded up to 128, / 128.
-//    Padding rows and samples are zero.  Any number of operands can share one
+//    Padding samples (beyond m) are zero; padding rows (beyond n) are not
+//    written and hold whatever the buffer held: every consumer masks them.  Any number of operands can share one
 //    buffer (each at its own first row), so one 2-D TMA descriptor of width
 //    128 bytes reaches every tile of every dataset.
 // Bp (popcount operand): one row per variable, bit (r % 32) of 32-bit word

@@ -1,7 +1,10 @@
 // Pack pass: one read of X (m samples x n variables, row-major uint8) writes
 //   P  - the transposed FP8 operand of the tensor-core Gram in K-block-major
 //        order (for each block of 128 samples, one 128-byte row per variable;
-//        0x00 / 0x38 = E4M3 1.0 per sample), padding zeroed,
+//        0x00 / 0x38 = E4M3 1.0 per sample), samples beyond m zeroed (they
+//        would add to every count); rows beyond n are not written (a garbage
+//        operand row only reaches accumulator rows or columns that every
+//        epilogue masks),
 //   Bp - the transposed bit-packed operand of the popcount Gram,
 //   v  - the column counts v_j = sum_r X_rj (Sec. 3.1, Term 2: v = D^T 1;
 //        also the diagonal of G11, Sec. 2 step 3).
@@ -191,7 +194,7 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int64_t j = j0 + colw * 4 + c;
-            if (j >= a.rows_p) continue;
+            if (j >= a.n) continue;   // padding rows are left as they are: masked downstream
             if (a.P != nullptr) {
                 uint4 o;
                 o.x = col[c][0] * 0x38u;
@@ -335,7 +338,9 @@ colsum_kernel(const uint8_t* __restrict__ X, int64_t m, int64_t n, int64_t rows_
 
 int64_t pack_job_ctas(PackJob& a) {
     const int64_t tiles_total = a.ldp / kTileR;
-    a.gx = static_cast<int32_t>(a.rows_p / kTileJ);
+    // column blocks holding variables; the operand's padding rows (n .. rows_p)
+    // are never written: every consumer masks rows and columns beyond n
+    a.gx = static_cast<int32_t>((a.n + kTileJ - 1) / kTileJ);
     // Tiles per CTA: at most kTilesPerCta, fewer when the job has few column
     // blocks, so that a job alone still launches about kPackCtasTarget CTAs
     // (enough loads in flight to stream HBM); more for very long sample ranges,
