@@ -17,7 +17,11 @@ timed on the host cores on a bounded sample of pairs, the batching workload
 (512 uneven datasets in one grouped graph vs separate calls) and the serving
 workload (Poisson arrivals at 200 req/s of mixed all-pairs / cross requests
 through the native server under a 40 GB budget: p50/p99 latency, and the
-capacity of a burst of requests under continuous batching).
+capacity of a burst of requests under continuous batching), the out-of-core
+output (n = 50,000 in row panels to host memory), the sparse (CSR) path at
+99-99.9% zeros, and the precision configuration (2^20 samples x 2^14
+variables: throughput and the largest error on sampled pairs against the
+FP64 oracle).
 
 --impl reference times the FP64 oracle (the only reference this method has:
 the paper ships no GPU code) on the host cores, each step a bounded sample of
@@ -431,6 +435,51 @@ def measure_out_of_core(dev, m=100_000, n=50_000, reps=2, seed=6):
     return res
 
 
+# --------------------------------------------------------------- precision configuration
+def measure_precision(dev, reps=3, check_pairs=256, use_oracle=True):
+    """All-pairs MI at 2^20 samples x 2^14 variables (one Gram launch: 2^20 < 2^24),
+    p_j ~ U(0.02, 0.5): fused throughput, tensor rate, and the largest |dMI| on seeded
+    sampled pairs against the FP64 oracle (the sampled columns are gathered on the device
+    and only they are copied to the host)."""
+    import torch
+
+    import simdata
+    from paper_2411_19702_gb300 import gbmi
+    r = simdata.PRECISION
+    X, _ = simdata.from_recipe(r, device=str(dev))
+    m, n = r.m, r.n
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    gbmi.mi_all_pairs(X, out=out, path="fused")
+    gbmi.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        gbmi.mi_all_pairs(X, out=out, path="fused")
+    e1.record()
+    torch.cuda.synchronize(dev)
+    gbmi.sync()
+    ms = e0.elapsed_time(e1) / reps
+    pairs = n * (n - 1) // 2
+    res = {"m": m, "n": n, "dist": "p_j ~ U(0.02, 0.5), iid Bernoulli", "ms_per_step": ms,
+           "pairs_per_s": pairs / (ms * 1e-3),
+           "tflops_step": float(m) * n * n / (ms * 1e-3) / 1e12}
+    if use_oracle:
+        import oracle
+        pi, pj = simdata.sample_pairs(n, n, check_pairs, 31)
+        pi = np.concatenate([pi, np.arange(0, n, n // 16)])      # a few diagonal entries
+        pj = np.concatenate([pj, np.arange(0, n, n // 16)])
+        cols, inv = np.unique(np.concatenate([pi, pj]), return_inverse=True)
+        sub = X[:, torch.from_numpy(cols).to(dev)].cpu().numpy()
+        _, want = oracle.mi_pairs(sub, inv[:len(pi)], inv[len(pi):])
+        got = out[torch.from_numpy(pi).to(dev), torch.from_numpy(pj).to(dev)].double().cpu()
+        err = float(np.max(np.abs(got.numpy() - want)))
+        res["parity"] = {"pairs": int(len(pi)), "max_abs_err_vs_oracle": err,
+                         "tolerance": 1e-6, "ok": err <= 1e-6}
+    del X, out
+    torch.cuda.empty_cache()
+    return res
+
+
 # --------------------------------------------------------------- sparse input
 def measure_sparse(dev, m=100_000, n=10_000, densities=(0.01, 0.005, 0.001), reps=3, seed=7):
     """Paper-shape inputs at 99%, 99.5% and 99.9% zeros (iid Bernoulli): the CSR path
@@ -781,6 +830,9 @@ def run_ours(args):
     batch = None
     if not args.skip_batch:
         batch = measure_batch(dev)
+    precision = None
+    if not args.skip_precision and rank == 0:
+        precision = measure_precision(dev, use_oracle=not args.skip_oracle)
     sparse = None
     if not args.skip_sparse and rank == 0:
         sparse = measure_sparse(dev)
@@ -835,6 +887,7 @@ def run_ours(args):
         "serving": serving,
         "out_of_core": out_of_core,
         "sparse": sparse,
+        "precision_config": precision,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
@@ -861,6 +914,7 @@ def main():
     ap.add_argument("--skip-ooc", action="store_true")
     ap.add_argument("--skip-sparse", action="store_true")
     ap.add_argument("--skip-library", action="store_true")
+    ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
