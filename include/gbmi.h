@@ -50,8 +50,10 @@ typedef enum {
 } gbmi_status;
 
 /* Computation paths.  AUTO picks the fused tensor-core path, or the popcount
- * path for tiny shapes, or the plain path when m is beyond the fused path's
- * exact-count limit. */
+ * path for tiny shapes.  The tensor-core Gram counts exactly in FP32 up to
+ * 2^24 samples per launch; beyond that it runs in sample chunks of 2^24,
+ * accumulating int32 counts in its workspace (n1 * n2 * 4 bytes), and the
+ * fused path evaluates MI in the last chunk's epilogue. */
 typedef enum {
     GBMI_PATH_AUTO = 0,
     GBMI_PATH_FUSED = 1,     /* tcgen05 FP8 Gram with the MI epilogue fused (one pass)      */
@@ -157,7 +159,7 @@ gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t n, float* 
  * [i0, i1) x columns [i0, n) and writes the mirror of that block as well, so
  * every off-diagonal pair is evaluated once.  Values are bit-identical to
  * mi_all_pairs / mi_cross.  Synchronous: returns when host_out is complete.
- * Needs m <= 2^24 (the fused path's exact FP32 range). */
+ * Needs m <= 2^24 (each panel is one exact Gram launch). */
 gbmi_status gbmi_mi_all_pairs_to_host(const uint8_t* X, int64_t m, int64_t n, float* host_out,
                                       int64_t panel_rows);
 gbmi_status gbmi_mi_cross_to_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,

@@ -120,8 +120,11 @@ bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn) {
     return pair_sms >= std::min<int64_t>(single_tiles, c.sm_count);
 }
 
-// Run the tensor-core Gram of one job over [0, m) in exact chunks.  mode MI
-// needs one chunk (m <= 2^24); the counts modes add chunk results into out_c.
+// Run the tensor-core Gram of one job over [0, m) in exact chunks of at most
+// 2^24 samples.  The counts modes add chunk results into out_c.  Mode MI with
+// several chunks accumulates the earlier chunks' exact int32 counts in the
+// workspace (counts, then counts-add) and runs the MI epilogue on the last
+// chunk with those counts added to its accumulator.
 // direct: the operands are the caller's matrices through *dmaps (no pack).
 gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int64_t m,
                      int mode, const OperandMaps* dmaps = nullptr) {
@@ -154,14 +157,25 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     L.counter = static_cast<unsigned int*>(c.sched.p);
     const int64_t kb_total = pack_ld(m) / kTcBK;
     const int64_t kb_chunk = kExactChunk / kTcBK;
-    if (mode == kTcModeMI && kb_total > kb_chunk)
-        return fail(GBMI_ERR_ARG, "fused path needs m <= 2^24");
+    int32_t* prefix = nullptr;   // MI over several chunks: counts of the earlier ones
+    if (mode == kTcModeMI && kb_total > kb_chunk) {
+        GBMI_TRY(ensure(c.counts, static_cast<size_t>(proto.n_a) * proto.n_b * 4,
+                        "count matrix"));
+        prefix = static_cast<int32_t*>(c.counts.p);
+    }
     const int grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, tiles))
                           : rt::grid_for(c, tiles);
     for (int64_t k0 = 0; k0 < kb_total; k0 += kb_chunk) {
         L.job0.k_begin = static_cast<int32_t>(k0);
         L.job0.k_blocks = static_cast<int32_t>(std::min(kb_chunk, kb_total - k0));
-        L.mode = (mode == kTcModeMI) ? kTcModeMI : (k0 == 0 ? kTcModeCounts : kTcModeCountsAdd);
+        if (mode == kTcModeMI) {
+            const bool last = k0 + kb_chunk >= kb_total;
+            L.mode = last ? kTcModeMI : (k0 == 0 ? kTcModeCounts : kTcModeCountsAdd);
+            L.job0.out_f = last ? proto.out_f : nullptr;
+            L.job0.out_c = prefix;   // counts target, then the MI epilogue's prefix
+        } else {
+            L.mode = k0 == 0 ? kTcModeCounts : kTcModeCountsAdd;
+        }
         GBMI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
         GBMI_LAUNCH(launch_gram_tc(maps, L, grid, g_stream),
                     L.mode == kTcModeMI ? "gram_tc_fused_mi" : "gram_tc_counts");
@@ -172,7 +186,6 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
 int choose_path(int path, int64_t m, int64_t n1, int64_t n2) {
     if (path != GBMI_PATH_AUTO) return path;
     if (static_cast<double>(m) * n1 * n2 <= kTinyWork) return GBMI_PATH_POPCOUNT;
-    if (m > kExactChunk) return GBMI_PATH_PLAIN;
     return GBMI_PATH_FUSED;
 }
 
@@ -282,8 +295,6 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
     GBMI_TRY(rt::get_ctx(&cp));
     DeviceCtx& c = *cp;
     path = choose_path(path, m, n1, n2);
-    if (path == GBMI_PATH_FUSED && m > kExactChunk)
-        return fail(GBMI_ERR_ARG, "the fused path needs m <= 2^24; use the plain path");
 
     if (path == GBMI_PATH_POPCOUNT) {
         const int64_t ldp = pack_ld(m);
@@ -647,7 +658,10 @@ gbmi_status host_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,
     DeviceCtx* cp = nullptr;
     GBMI_TRY(rt::get_ctx(&cp));
     DeviceCtx& c = *cp;
-    if (choose_path(GBMI_PATH_AUTO, m, n1, n2) == GBMI_PATH_FUSED && !g_opt.direct)
+    // the pipelined form splits the Gram at upload-chunk boundaries: one
+    // exact chunk of at most 2^24 samples per launch is guaranteed only below it
+    if (choose_path(GBMI_PATH_AUTO, m, n1, n2) == GBMI_PATH_FUSED && !g_opt.direct &&
+        m <= kExactChunk)
         return host_pipelined(c, X, Y, m, n1, n2, out, sym);
     const size_t xb = static_cast<size_t>(m) * n1, yb = static_cast<size_t>(m) * n2;
     const size_t ob = static_cast<size_t>(n1) * n2 * 4;

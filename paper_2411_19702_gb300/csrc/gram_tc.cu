@@ -552,9 +552,11 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
 #pragma unroll
                 for (int q = 0; q < kGroup; ++q) {
                     const int64_t j = j0 + q;
-                    const int32_t n11 = __float2int_rn(__uint_as_float(r[q]) * cscale);
+                    int32_t n11 = __float2int_rn(__uint_as_float(r[q]) * cscale);
                     float mi = 0.f;
                     if (row_ok && j < n_b && (!sym || j >= i)) {
+                        // counts of earlier sample chunks (or null)
+                        if (job.out_c != nullptr) n11 += job.out_c[i * job.ld_out + j];
                         const MiVar B = cv[g + q];
                         const MiCounts c = mi_counts(n11, A.v, B.v, P);
                         if (c.det != 0) {

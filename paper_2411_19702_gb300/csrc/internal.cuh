@@ -135,8 +135,8 @@ struct GramJob {
     const MiVar* va;           // per-variable terms (MI mode)
     const MiVar* vb;
     float* out_f;
-    int32_t* out_c;            // counts modes: output; MI with the FP32 epilogue: counts of
-                               // earlier sample chunks added to this launch's (or null)
+    int32_t* out_c;            // counts modes: output; MI modes: counts of earlier sample
+                               // chunks added to this launch's (or null)
     int64_t ld_out;
     float* out_t;              // MI mode, or null: also write (j, i) to out_t[j * ld_t + i]
     int64_t ld_t;

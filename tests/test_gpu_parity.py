@@ -237,9 +237,10 @@ def test_argument_errors():
     # output overlapping the input
     assert lib.mi_all_pairs(X.data_ptr(), 10, 4, X.data_ptr()) == gbmi.ERR_ARG
     assert lib.gbmi_mi_all_pairs_path(X.data_ptr(), 10, 4, out.data_ptr(), 9) == gbmi.ERR_ARG
-    big = torch.zeros((1 << 12, 4), dtype=torch.uint8, device="cuda")
-    # the fused path refuses m > 2^24 (checked before touching memory)
-    assert lib.gbmi_mi_all_pairs_path(big.data_ptr(), (1 << 24) + 1, 4, out.data_ptr(),
+    # empty shapes are refused before anything is launched
+    assert lib.gbmi_mi_all_pairs_path(X.data_ptr(), 0, 4, out.data_ptr(),
+                                      gbmi.PATH_FUSED) == gbmi.ERR_ARG
+    assert lib.gbmi_mi_all_pairs_path(X.data_ptr(), 10, 0, out.data_ptr(),
                                       gbmi.PATH_FUSED) == gbmi.ERR_ARG
 
 
