@@ -19,9 +19,9 @@ workload (Poisson arrivals at 200 req/s of mixed all-pairs / cross requests
 through the native server under a 40 GB budget: p50/p99 latency, and the
 capacity of a burst of requests under continuous batching), the out-of-core
 output (n = 50,000 in row panels to host memory), the sparse (CSR) path at
-99-99.9% zeros, and the precision configuration (2^20 samples x 2^14
-variables: throughput and the largest error on sampled pairs against the
-FP64 oracle).
+99-99.9% zeros, cross MI between X and a second matrix of the same shape,
+and the precision configuration (2^20 samples x 2^14 variables: throughput
+and the largest error on sampled pairs against the FP64 oracle).
 
 --impl reference times the FP64 oracle (the only reference this method has:
 the paper ships no GPU code) on the host cores, each step a bounded sample of
@@ -435,6 +435,57 @@ def measure_out_of_core(dev, m=100_000, n=50_000, reps=2, seed=6):
     return res
 
 
+# --------------------------------------------------------------- cross MI
+def measure_cross(dev, X, reps=5, seed=8, check_pairs=256, use_oracle=True):
+    """mi_cross between the workload's X and a second seeded matrix Y of the same shape
+    (n1 = n2 = n: every one of the n^2 pairs is computed, none mirrored), fused path; the
+    parity sample includes the planted (X column, Y column) pairs."""
+    import torch
+
+    import simdata
+    from paper_2411_19702_gb300 import gbmi
+    m, n = X.shape
+    Y, _ = simdata.make(m, n, seed, "beta", 0.0, 0.05, device=str(dev))
+    # 1% of Y's columns are noisy copies (flip probability 0.05) of seeded columns of X
+    rng = np.random.Generator(np.random.PCG64([seed, 3]))
+    yc = rng.choice(n, size=max(1, n // 100), replace=False)
+    xc = rng.choice(n, size=yc.size, replace=False)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed + 1000)
+    for a, b in zip(yc.tolist(), xc.tolist()):
+        flip = (torch.rand(m, generator=g, device=dev) < 0.05).to(torch.uint8)
+        Y[:, a] = X[:, b] ^ flip
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    gbmi.mi_cross(X, Y, out=out, path="fused")
+    gbmi.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        gbmi.mi_cross(X, Y, out=out, path="fused")
+    e1.record()
+    torch.cuda.synchronize(dev)
+    gbmi.sync()
+    ms = e0.elapsed_time(e1) / reps
+    res = {"m": m, "n1": n, "n2": n, "pairs": n * n, "ms_per_step": ms,
+           "pairs_per_s": n * n / (ms * 1e-3), "tflops_step": 2.0 * m * n * n / (ms * 1e-3) / 1e12}
+    if use_oracle:
+        import oracle
+        pi, pj = simdata.sample_pairs(n, n, check_pairs, 41, symmetric=False)
+        pi, pj = np.concatenate([pi, xc]), np.concatenate([pj, yc])   # with the planted pairs
+        a_cols, ia = np.unique(pi, return_inverse=True)
+        b_cols, ib = np.unique(pj, return_inverse=True)
+        A = X[:, torch.from_numpy(a_cols).to(dev)].cpu().numpy()
+        B = Y[:, torch.from_numpy(b_cols).to(dev)].cpu().numpy()
+        _, want = oracle.mi_pairs(A, ia, ib, Y=B)
+        got = out[torch.from_numpy(pi).to(dev), torch.from_numpy(pj).to(dev)].double().cpu()
+        err = float(np.max(np.abs(got.numpy() - want)))
+        res["parity"] = {"pairs": int(len(pi)), "max_abs_err_vs_oracle": err,
+                         "tolerance": 1e-6, "ok": err <= 1e-6}
+    del Y, out
+    torch.cuda.empty_cache()
+    return res
+
+
 # --------------------------------------------------------------- precision configuration
 def measure_precision(dev, reps=3, check_pairs=256, use_oracle=True):
     """All-pairs MI at 2^20 samples x 2^14 variables (one Gram launch: 2^20 < 2^24),
@@ -830,6 +881,9 @@ def run_ours(args):
     batch = None
     if not args.skip_batch:
         batch = measure_batch(dev)
+    cross = None
+    if not args.skip_cross and rank == 0:
+        cross = measure_cross(dev, X, use_oracle=not args.skip_oracle)
     precision = None
     if not args.skip_precision and rank == 0:
         precision = measure_precision(dev, use_oracle=not args.skip_oracle)
@@ -887,6 +941,7 @@ def run_ours(args):
         "serving": serving,
         "out_of_core": out_of_core,
         "sparse": sparse,
+        "cross": cross,
         "precision_config": precision,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -915,6 +970,7 @@ def main():
     ap.add_argument("--skip-sparse", action="store_true")
     ap.add_argument("--skip-library", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
+    ap.add_argument("--skip-cross", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
