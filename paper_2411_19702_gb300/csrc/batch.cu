@@ -23,7 +23,7 @@ struct gbmi_batch {
     int device = -1;
     int k = 0;
     std::vector<gbmi_job> jobs;
-    gbmi::rt::DevBuf P, v, vars, packjobs, varbegin, params, gramjobs, tiles, sched;
+    gbmi::rt::DevBuf P, v, vars, packjobs, ctajob, varbegin, params, gramjobs, tiles, sched;
     std::vector<gbmi::PackJob> hpack;
     std::vector<int64_t> hvarbegin;
     std::vector<gbmi::MiParams> hparams;
@@ -77,7 +77,7 @@ void release_plan(gbmi_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    for (rt::DevBuf* d : {&b->P, &b->v, &b->vars, &b->packjobs, &b->varbegin, &b->params,
+    for (rt::DevBuf* d : {&b->P, &b->v, &b->vars, &b->packjobs, &b->ctajob, &b->varbegin, &b->params,
                           &b->gramjobs, &b->tiles, &b->sched})
         rt::release(*d);
 }
@@ -85,7 +85,8 @@ void release_plan(gbmi_batch* b) {
 gbmi_status enqueue(gbmi_batch* b, cudaStream_t s, unsigned int* err) {
     GBMI_CUDA(launch_zero_u32(b->v.p, b->total_vars, s), "batch zero");
     GBMI_CUDA(launch_pack_grouped(static_cast<const PackJob*>(b->packjobs.p),
-                                  static_cast<int>(b->hpack.size()), b->total_ctas, s),
+                                  static_cast<int>(b->hpack.size()), b->total_ctas,
+                                  static_cast<const int32_t*>(b->ctajob.p), s),
               "batch pack");
     GBMI_CUDA(launch_mi_vars_grouped(static_cast<const int32_t*>(b->v.p),
                                      static_cast<const int64_t*>(b->varbegin.p),
@@ -221,9 +222,16 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
         pj.P = Pb + reinterpret_cast<uintptr_t>(pj.P);
         pj.v = vb + reinterpret_cast<uintptr_t>(pj.v) / 4;
         pj.cta_begin = ctas;
-        ctas += pack_job_ctas(pj);
+        ctas += pack_job_ctas(pj, true);
     }
     b->total_ctas = ctas;
+    // CTA -> pack job table of the grouped pack
+    std::vector<int32_t> cta_job(static_cast<size_t>(ctas));
+    for (size_t q = 0; q < b->hpack.size(); ++q) {
+        const int64_t e = q + 1 < b->hpack.size() ? b->hpack[q + 1].cta_begin : ctas;
+        std::fill(cta_job.begin() + b->hpack[q].cta_begin, cta_job.begin() + e,
+                  static_cast<int32_t>(q));
+    }
     for (GramJob& g : b->hgram) {
         g.va = varsb + reinterpret_cast<uintptr_t>(g.va) / sizeof(MiVar);
         g.vb = varsb + reinterpret_cast<uintptr_t>(g.vb) / sizeof(MiVar);
@@ -280,6 +288,9 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
     b->pair_grid = 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, npair));
 
     st = upload(b->packjobs, b->hpack.data(), b->hpack.size() * sizeof(PackJob), "batch pack table");
+    if (st == GBMI_OK && ctas > 0)
+        st = upload(b->ctajob, cta_job.data(), cta_job.size() * sizeof(int32_t),
+                    "batch pack CTA table");
     if (st == GBMI_OK)
         st = upload(b->varbegin, b->hvarbegin.data(), b->hvarbegin.size() * sizeof(int64_t),
                     "batch variable ranges");

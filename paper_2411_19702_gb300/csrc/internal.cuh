@@ -58,10 +58,13 @@ struct PackJob {
     int32_t pad;
 };
 // Fill the launch fields (gx, tpc, vec) of a job; returns its CTA count.
-int64_t pack_job_ctas(PackJob& j);
+// grouped: the job is one of many in a grouped launch (the most tiles per CTA).
+int64_t pack_job_ctas(PackJob& j, bool grouped = false);
 cudaError_t launch_pack(const PackJob& job, cudaStream_t s);
+// Grouped pack: CTA c works for job cta_job[c] (device table), or, with a null
+// table, for the last job whose cta_begin <= c (binary search).
 cudaError_t launch_pack_grouped(const PackJob* jobs, int njobs, int64_t total_ctas,
-                                cudaStream_t s);
+                                const int32_t* cta_job, cudaStream_t s);
 cudaError_t launch_validate(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
                             unsigned int* flag, cudaStream_t s);
 // Column counts of X for the direct operand path (n % 16 == 0, X 16-byte

@@ -237,13 +237,18 @@ pack_kernel(const PackJob job) {
 }
 
 __global__ void __launch_bounds__(kPackThreads, 4)
-pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs) {
+pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs,
+                    const int32_t* __restrict__ cta_job) {
     __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
     const int64_t c = blockIdx.x;
     int lo = 0, hi = njobs - 1;   // last job whose cta_begin <= c
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].cta_begin <= c) lo = mid; else hi = mid - 1;
+    if (cta_job != nullptr) {
+        lo = __ldg(cta_job + c);
+    } else {
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].cta_begin <= c) lo = mid; else hi = mid - 1;
+        }
     }
     const PackJob job = jobs[lo];
     const int64_t cl = c - job.cta_begin;
@@ -336,7 +341,7 @@ colsum_kernel(const uint8_t* __restrict__ X, int64_t m, int64_t n, int64_t rows_
 
 }  // namespace
 
-int64_t pack_job_ctas(PackJob& a) {
+int64_t pack_job_ctas(PackJob& a, bool grouped) {
     const int64_t tiles_total = a.ldp / kTileR;
     // column blocks holding variables; the operand's padding rows (n .. rows_p)
     // are never written: every consumer masks rows and columns beyond n
@@ -344,8 +349,11 @@ int64_t pack_job_ctas(PackJob& a) {
     // Tiles per CTA: at most kTilesPerCta, fewer when the job has few column
     // blocks, so that a job alone still launches about kPackCtasTarget CTAs
     // (enough loads in flight to stream HBM); more for very long sample ranges,
-    // to keep the CTA count moderate.
-    int64_t tpc = (tiles_total * a.gx + kPackCtasTarget - 1) / kPackCtasTarget;
+    // to keep the CTA count moderate.  In a grouped launch the other jobs
+    // supply the CTAs, and every CTA takes the most tiles (a CTA of one small
+    // item would spend about as long starting as packing).
+    int64_t tpc = grouped ? kTilesPerCta
+                          : (tiles_total * a.gx + kPackCtasTarget - 1) / kPackCtasTarget;
     tpc = tpc < 1 ? 1 : (tpc > kTilesPerCta ? kTilesPerCta : tpc);
     while ((tiles_total + tpc - 1) / tpc > (int64_t{1} << 16)) tpc *= 2;
     a.tpc = static_cast<int32_t>(tpc);
@@ -367,10 +375,11 @@ cudaError_t launch_pack(const PackJob& job, cudaStream_t s) {
 }
 
 cudaError_t launch_pack_grouped(const PackJob* jobs, int njobs, int64_t total_ctas,
-                                cudaStream_t s) {
+                                const int32_t* cta_job, cudaStream_t s) {
     if (njobs <= 0 || total_ctas <= 0) return cudaSuccess;
     if (total_ctas > 0x7FFFFFFF) return cudaErrorInvalidValue;
-    pack_grouped_kernel<<<static_cast<unsigned>(total_ctas), kPackThreads, 0, s>>>(jobs, njobs);
+    pack_grouped_kernel<<<static_cast<unsigned>(total_ctas), kPackThreads, 0, s>>>(jobs, njobs,
+                                                                                   cta_job);
     return cudaGetLastError();
 }
 

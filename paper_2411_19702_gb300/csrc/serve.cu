@@ -315,7 +315,7 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
 
     if (!pj.empty()) {
         GBMI_CUDA(launch_pack_grouped(static_cast<const PackJob*>(sl.dpack.p),
-                                      static_cast<int>(pj.size()), ctas, sl.s),
+                                      static_cast<int>(pj.size()), ctas, nullptr, sl.s),
                   "serve pack");
         for (int64_t id : sl.packs) {
             const Dataset& d = S->datasets[id];
