@@ -27,8 +27,11 @@ and the largest error on sampled pairs against the FP64 oracle).
 the paper ships no GPU code) on the host cores, each step a bounded sample of
 the same workload's pairs.
 
-Multi-GPU (torchrun): every rank runs its own replica of the workload (weak
-scaling, no collective on the data path); value = all ranks' pairs / max time.
+Multi-GPU (torchrun): by default every rank runs its own replica of the
+workload (weak scaling, no collective on the data path); value = all ranks'
+pairs / max time.  --scaling strong splits the one workload instead: rank r
+computes shard r of N of the fused Gram's tile list (gbmi_mi_all_pairs_shard,
+no collective either); value = the workload's pairs / max time.
 """
 from __future__ import annotations
 
@@ -75,9 +78,20 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     return world * units_per_rank / seconds_max
 
 
+def strong_rate(units_total: float, seconds_max: float) -> float:
+    """Whole-job throughput of one problem split over the ranks: its units / slowest time."""
+    return units_total / seconds_max
+
+
 def replica_seed(base: int, rank: int) -> int:
     """Seed of rank `rank`'s replica: every rank solves its own independent problem."""
     return base + rank
+
+
+def workload_seed(base: int, rank: int, strong: bool) -> int:
+    """Strong scaling splits one problem (the same input on every rank); weak scaling
+    gives every rank its own replica."""
+    return base if strong else replica_seed(base, rank)
 
 
 def _workload(m, n):
@@ -750,13 +764,20 @@ def run_ours(args):
     def reduce_max(x):
         return max_over_ranks(x, dist, dev)
 
-    X, info = simdata.make(m, n, replica_seed(simdata.PAPER.seed, rank), "beta", 0.01, 0.05,
-                           device=str(dev))
+    strong = args.scaling == "strong"
+    seed = workload_seed(simdata.PAPER.seed, rank, strong)
+    X, info = simdata.make(m, n, seed, "beta", 0.01, 0.05, device=str(dev))
     out = torch.empty((n, n), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(path="fused"):
-        gbmi.mi_all_pairs(X, out=out, path=path)
+        if strong and world > 1 and path == "fused":
+            gbmi.mi_all_pairs_shard(X, rank, world, out=out)
+        else:
+            gbmi.mi_all_pairs(X, out=out, path=path)
+
+    def rate(ms):   # whole-job pairs/s from the slowest rank's time per step
+        return strong_rate(pairs, ms * 1e-3) if strong else whole_job_rate(pairs, world, ms * 1e-3)
 
     def timed(path, steps, warmup, sample_clocks=False, profile=False):
         for _ in range(warmup):
@@ -799,7 +820,7 @@ def run_ours(args):
     XT = None
     if rank == 0 and not args.skip_oracle:
         import oracle
-        step("fused")
+        gbmi.mi_all_pairs(X, out=out, path="fused")   # the whole matrix, also when sharded
         gbmi.sync()
         XT = oracle.transpose(X.cpu().numpy())
         pi, pj = simdata.sample_pairs(n, n, 2000, 99)
@@ -831,7 +852,7 @@ def run_ours(args):
     peaks = _peaks()
     gram = prof.get("gram_tc_fused_mi", {"ms": float("nan"), "launches": 1})
     gram_ms = gram["ms"] / max(gram["launches"], 1)
-    flops = float(m) * n * n
+    flops = float(m) * n * n / (world if strong else 1)   # a shard's launch does its share
     achieved = flops / (gram_ms * 1e-3) / 1e12
     peak = 2.0 * peaks["bf16_tflops"]           # FP8 = 2 x measured BF16 (nominal ratio)
     traffic, tsrc = _profiled_traffic()
@@ -856,7 +877,9 @@ def run_ours(args):
 
     # end to end through the host-buffer C-ABI call (pinned buffers)
     e2e = None
-    if not args.skip_e2e:
+    if strong and world > 1:
+        e2e = {"unavailable": "strong scaling: the host-buffer call is not sharded"}
+    elif not args.skip_e2e:
         Xh = X.cpu().pin_memory()
         outh = torch.empty((n, n), dtype=torch.float32).pin_memory()
         gbmi.mi_all_pairs_host(Xh, outh)
@@ -897,26 +920,26 @@ def run_ours(args):
     if not args.skip_serve and rank == 0:
         serving = measure_serving(dev, seconds=args.serve_seconds)
 
-    value = whole_job_rate(pairs, world, fused_ms * 1e-3)
+    value = rate(fused_ms)
     plain_ms = reduce_max(plain["ms"])
     popc_ms = reduce_max(popc["ms"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": fused_ms,
-        "higher_is_better": True, "scaling": "weak",
+        "higher_is_better": True, "scaling": args.scaling,
         "vs_baseline": value / (pairs / PAPER_OPT_T_S),
         "dtype": "e4m3", "data": "synthetic",
         "config": dict(_workload(m, n), path="fused",
                        arithmetic="FP8 E4M3 0/1 operands, FP32 tensor-core accumulation "
                                   "(exact counts), FP32 epilogue, FP64 combine below 1e-4"),
-        "plain": {"value": whole_job_rate(pairs, world, plain_ms * 1e-3), "ms_per_step": plain_ms,
+        "plain": {"value": rate(plain_ms), "ms_per_step": plain_ms,
                   "path": "tcgen05 Gram -> int32 N11 in HBM -> elementwise MI kernel",
                   "kernels": {k: v["ms"] / max(v["launches"], 1)
                               for k, v in (plain["profile"] or {}).items()}},
         "fixup_toggled": {"fp64_combine": bool(1 - fix_default),
-                          "value": whole_job_rate(pairs, world, reduce_max(alt["ms"]) * 1e-3),
+                          "value": rate(reduce_max(alt["ms"])),
                           "ms_per_step": reduce_max(alt["ms"])},
-        "popcount": {"value": whole_job_rate(pairs, world, popc_ms * 1e-3), "ms_per_step": popc_ms,
+        "popcount": {"value": rate(popc_ms), "ms_per_step": popc_ms,
                      "roofline": {"bound": "alu", "achieved": popc_rate / 1e12,
                                   "peak": popc_peak / 1e12, "unit": "Tpopc/s",
                                   "frac": popc_rate / popc_peak,
@@ -971,6 +994,7 @@ def main():
     ap.add_argument("--skip-library", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--skip-cross", action="store_true")
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:

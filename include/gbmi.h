@@ -104,6 +104,19 @@ gbmi_status mi_all_pairs(const uint8_t* X, int64_t m, int64_t n, float* out);
 gbmi_status mi_cross(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
                      float* out);
 
+/* One shard of mi_all_pairs on the fused path, for splitting one problem over
+ * several GPUs (one call per GPU, each with its own X copy and out buffer):
+ * the upper-triangle tile list of the Gram (the single call's list and order)
+ * is cut into num_shards contiguous shares of equal tile count, and this call
+ * computes share `shard` (0 <= shard < num_shards), writing out[i*n + j] and
+ * out[j*n + i] for the pairs of its tiles only; other entries are untouched.
+ * The shards' writes together are exactly mi_all_pairs's output.  Pack and
+ * per-variable terms are computed in full by every shard (the Gram dominates).
+ * Same limits and errors as mi_all_pairs, plus GBMI_ERR_ARG for a shard out
+ * of range.  The paper has no counterpart: its method runs on one device. */
+gbmi_status gbmi_mi_all_pairs_shard(const uint8_t* X, int64_t m, int64_t n, float* out,
+                                    int shard, int num_shards);
+
 /* The same two calls with an explicit path (gbmi_path). */
 gbmi_status gbmi_mi_all_pairs_path(const uint8_t* X, int64_t m, int64_t n, float* out, int path);
 gbmi_status gbmi_mi_cross_path(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1,

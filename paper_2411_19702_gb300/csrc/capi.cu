@@ -126,8 +126,12 @@ bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn) {
 // workspace (counts, then counts-add) and runs the MI epilogue on the last
 // chunk with those counts added to its accumulator.
 // direct: the operands are the caller's matrices through *dmaps (no pack).
+// Shard `shard` of `num_shards` runs only that contiguous share of the tile
+// list (the same list and order as the whole problem), so the shards' writes
+// together are the whole result.
 gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int64_t m,
-                     int mode, const OperandMaps* dmaps = nullptr) {
+                     int mode, const OperandMaps* dmaps = nullptr, int shard = 0,
+                     int num_shards = 1) {
     OperandMaps maps;
     if (dmaps != nullptr)
         maps = *dmaps;
@@ -147,8 +151,11 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     L.job0.bn = bn;
     L.pair = pair ? 1 : 0;
     L.fixup = proto.mp.fixup;
-    L.tiles = static_cast<const GramTile*>(c.tiles.p);
-    L.num_tiles = tiles;
+    const int64_t t0 = static_cast<int64_t>(tiles) * shard / num_shards;
+    const int64_t t1 = static_cast<int64_t>(tiles) * (shard + 1) / num_shards;
+    L.tiles = static_cast<const GramTile*>(c.tiles.p) + t0;
+    L.num_tiles = static_cast<int>(t1 - t0);
+    tiles = L.num_tiles;
     L.err = static_cast<unsigned int*>(c.err.p);
     L.timeout_ns = g_opt.timeout_ns;
     L.debug_flags = g_opt.debug_flags;
@@ -281,8 +288,9 @@ GramJob tc_job(const TcLayout& L, int64_t m, int64_t n1, int64_t n2, bool sym, i
 }
 
 // MI between the variables of X (n1) and Y (n2, or X itself when sym).
+// num_shards > 1 (fused path only): just shard `shard` of the Gram's tiles.
 gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, int64_t n2,
-                    float* out, int path, bool sym) {
+                    float* out, int path, bool sym, int shard = 0, int num_shards = 1) {
     if (X == nullptr || out == nullptr || (!sym && Y == nullptr))
         return fail(GBMI_ERR_ARG, "null pointer");
     GBMI_TRY(check_sizes(m, n1, n2));
@@ -295,6 +303,9 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
     GBMI_TRY(rt::get_ctx(&cp));
     DeviceCtx& c = *cp;
     path = choose_path(path, m, n1, n2);
+    if (num_shards < 1 || shard < 0 || shard >= num_shards)
+        return fail(GBMI_ERR_ARG, "shard must be in [0, num_shards)");
+    if (num_shards > 1) path = GBMI_PATH_FUSED;
 
     if (path == GBMI_PATH_POPCOUNT) {
         const int64_t ldp = pack_ld(m);
@@ -322,7 +333,7 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
         const int bn = rt::choose_bn(m, n1, n2, sym);
         if (path == GBMI_PATH_FUSED)
             return run_gram(c, L.total_rows, tc_job(L, m, n1, n2, sym, bn, va, vb, mp, out, nullptr),
-                            m, kTcModeMI, L.direct ? &L.maps : nullptr);
+                            m, kTcModeMI, L.direct ? &L.maps : nullptr, shard, num_shards);
         // plain: exact counts to HBM, then the elementwise MI kernel
         GBMI_TRY(ensure(c.counts, static_cast<size_t>(n1) * n2 * 4, "count matrix"));
         int32_t* N11 = static_cast<int32_t*>(c.counts.p);
@@ -935,6 +946,12 @@ gbmi_status gbmi_mi_cross_path(const uint8_t* X, const uint8_t* Y, int64_t m, in
                                int64_t n2, float* out, int path) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     return mi_impl(X, Y, m, n1, n2, out, path, false);
+}
+
+gbmi_status gbmi_mi_all_pairs_shard(const uint8_t* X, int64_t m, int64_t n, float* out,
+                                    int shard, int num_shards) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    return mi_impl(X, nullptr, m, n, n, out, GBMI_PATH_FUSED, true, shard, num_shards);
 }
 
 gbmi_status mi_all_pairs_host(const uint8_t* X, int64_t m, int64_t n, float* out) {

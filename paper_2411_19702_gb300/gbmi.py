@@ -61,6 +61,7 @@ def load(path: str | None = None):
             "mi_all_pairs": [vp, i64, i64, vp],
             "mi_cross": [vp, vp, i64, i64, i64, vp],
             "gbmi_mi_all_pairs_path": [vp, i64, i64, vp, i32],
+            "gbmi_mi_all_pairs_shard": [vp, i64, i64, vp, i32, i32],
             "gbmi_mi_cross_path": [vp, vp, i64, i64, i64, vp, i32],
             "mi_all_pairs_host": [vp, i64, i64, vp],
             "mi_cross_host": [vp, vp, i64, i64, i64, vp],
@@ -165,6 +166,23 @@ def mi_all_pairs(X, out=None, path="auto"):
         assert out.shape == (n, n) and out.dtype == torch.float32 and out.is_contiguous()
         lib = _bind_stream(X.device)
         _check(lib.gbmi_mi_all_pairs_path(X.data_ptr(), m, n, out.data_ptr(), _path(path)))
+    return out
+
+
+def mi_all_pairs_shard(X, shard, num_shards, out=None):
+    """Shard `shard` of `num_shards` of the fused all-pairs call: only the pairs of
+    that contiguous share of the Gram's tile list are written into out (n x n);
+    the shards' writes together are mi_all_pairs(X)'s output."""
+    import torch
+    X = _prep(X)
+    m, n = X.shape
+    with torch.cuda.device(X.device):
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float32, device=X.device)
+        assert out.shape == (n, n) and out.dtype == torch.float32 and out.is_contiguous()
+        lib = _bind_stream(X.device)
+        _check(lib.gbmi_mi_all_pairs_shard(X.data_ptr(), m, n, out.data_ptr(), int(shard),
+                                           int(num_shards)))
     return out
 
 

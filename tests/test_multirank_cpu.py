@@ -1,9 +1,10 @@
 """The N > 1 host path of the benchmark on CPU ranks (gloo, world size 2).
 
 With several GPUs every rank runs an independent replica (its own seed, no
-collective on the data path); the only cross-rank steps are the barrier and
-the maximum of the per-rank times, from which rank 0 reports the whole-job
-rate.  The reference arm runs on rank 0 alone.
+collective on the data path), or, with --scaling strong, its shard of one
+problem (the same input on every rank); the only cross-rank steps are the
+barrier and the maximum of the per-rank times, from which rank 0 reports the
+whole-job rate.  The reference arm runs on rank 0 alone.
 """
 from __future__ import annotations
 
@@ -39,8 +40,12 @@ def _rank_main(rank, world, port, q):
         dist.barrier()
         slowest = bench.max_over_ranks(local_s, dist, "cpu")
         rate = bench.whole_job_rate(1000, world, slowest)
+        srate = bench.strong_rate(1000, slowest)
         X, _ = simdata.make(64, 16, bench.replica_seed(2, rank), "beta", 0.0, 0.0, device="cpu")
-        q.put((rank, slowest, rate, np.asarray(X)[:8].tobytes()))
+        Xs, _ = simdata.make(64, 16, bench.workload_seed(2, rank, True), "beta", 0.0, 0.0,
+                             device="cpu")
+        q.put((rank, slowest, rate, np.asarray(X)[:8].tobytes(), srate,
+               np.asarray(Xs)[:8].tobytes()))
     finally:
         dist.destroy_process_group()
 
@@ -57,10 +62,12 @@ def test_max_over_ranks_and_whole_job_rate_gloo():
         p.join(timeout=60)
         assert p.exitcode == 0
     out.sort()
-    for rank, slowest, rate, _ in out:
+    for rank, slowest, rate, _, srate, _ in out:
         assert slowest == pytest.approx(0.020)        # every rank sees the slowest time
         assert rate == pytest.approx(2 * 1000 / 0.020)  # all ranks' units / slowest time
+        assert srate == pytest.approx(1000 / 0.020)     # one split problem's units
     assert out[0][3] != out[1][3]                      # replicas draw independent inputs
+    assert out[0][5] == out[1][5]                      # a split problem has one input
 
 
 def test_helpers_without_process_group():
@@ -68,6 +75,8 @@ def test_helpers_without_process_group():
     assert bench.max_over_ranks(1.5) == 1.5
     assert bench.whole_job_rate(10, 1, 2.0) == 5.0
     assert bench.replica_seed(2, 3) == 5
+    assert bench.workload_seed(2, 3, True) == 2 and bench.workload_seed(2, 3, False) == 5
+    assert bench.strong_rate(10, 2.0) == 5.0
 
 
 def test_reference_arm_runs_on_rank_zero_only():
