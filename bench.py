@@ -776,7 +776,7 @@ def run_ours(args):
         else:
             gbmi.mi_all_pairs(X, out=out, path=path)
 
-    def rate(ms):   # whole-job pairs/s from the slowest rank's time per step
+    def job_rate(ms):   # whole-job pairs/s from the slowest rank's time per step
         return strong_rate(pairs, ms * 1e-3) if strong else whole_job_rate(pairs, world, ms * 1e-3)
 
     def timed(path, steps, warmup, sample_clocks=False, profile=False):
@@ -920,7 +920,7 @@ def run_ours(args):
     if not args.skip_serve and rank == 0:
         serving = measure_serving(dev, seconds=args.serve_seconds)
 
-    value = rate(fused_ms)
+    value = job_rate(fused_ms)
     plain_ms = reduce_max(plain["ms"])
     popc_ms = reduce_max(popc["ms"])
     line = {
@@ -932,14 +932,14 @@ def run_ours(args):
         "config": dict(_workload(m, n), path="fused",
                        arithmetic="FP8 E4M3 0/1 operands, FP32 tensor-core accumulation "
                                   "(exact counts), FP32 epilogue, FP64 combine below 1e-4"),
-        "plain": {"value": rate(plain_ms), "ms_per_step": plain_ms,
+        "plain": {"value": job_rate(plain_ms), "ms_per_step": plain_ms,
                   "path": "tcgen05 Gram -> int32 N11 in HBM -> elementwise MI kernel",
                   "kernels": {k: v["ms"] / max(v["launches"], 1)
                               for k, v in (plain["profile"] or {}).items()}},
         "fixup_toggled": {"fp64_combine": bool(1 - fix_default),
-                          "value": rate(reduce_max(alt["ms"])),
+                          "value": job_rate(reduce_max(alt["ms"])),
                           "ms_per_step": reduce_max(alt["ms"])},
-        "popcount": {"value": rate(popc_ms), "ms_per_step": popc_ms,
+        "popcount": {"value": job_rate(popc_ms), "ms_per_step": popc_ms,
                      "roofline": {"bound": "alu", "achieved": popc_rate / 1e12,
                                   "peak": popc_peak / 1e12, "unit": "Tpopc/s",
                                   "frac": popc_rate / popc_peak,
