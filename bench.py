@@ -516,16 +516,23 @@ def measure_precision(dev, reps=3, check_pairs=256, use_oracle=True):
     out = torch.empty((n, n), dtype=torch.float32, device=dev)
     gbmi.mi_all_pairs(X, out=out, path="fused")
     gbmi.sync()
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        gbmi.mi_all_pairs(X, out=out, path="fused")
-    e1.record()
-    torch.cuda.synchronize(dev)
+    with ClockSampler(uuid) as clocks:
+        e0.record()
+        for _ in range(reps):
+            gbmi.mi_all_pairs(X, out=out, path="fused")
+        e1.record()
+        torch.cuda.synchronize(dev)
     gbmi.sync()
     ms = e0.elapsed_time(e1) / reps
     pairs = n * (n - 1) // 2
     res = {"m": m, "n": n, "dist": "p_j ~ U(0.02, 0.5), iid Bernoulli", "ms_per_step": ms,
+           "clocks": clocks.summary(),
            "pairs_per_s": pairs / (ms * 1e-3),
            "tflops_step": float(m) * n * n / (ms * 1e-3) / 1e12}
     if use_oracle:
