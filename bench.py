@@ -554,8 +554,9 @@ def measure_precision(dev, reps=3, check_pairs=256, use_oracle=True):
 
 # --------------------------------------------------------------- sparse input
 def measure_sparse(dev, m=100_000, n=10_000, densities=(0.01, 0.005, 0.001), reps=3, seed=7):
-    """Paper-shape inputs at 99%, 99.5% and 99.9% zeros (iid Bernoulli): the CSR path
-    (inputs resident in CSR) against the dense fused path on the same matrix."""
+    """Paper-shape inputs at 99%, 99.5% and 99.9% zeros (iid Bernoulli): the CSR call
+    (inputs resident in CSR) with pair enumeration forced and with the cost model's choice,
+    against the dense fused path on the same matrix."""
     import torch
 
     from paper_2411_19702_gb300 import gbmi
@@ -579,8 +580,15 @@ def measure_sparse(dev, m=100_000, n=10_000, densities=(0.01, 0.005, 0.001), rep
             torch.cuda.synchronize(dev)
             gbmi.sync()
             return e0.elapsed_time(e1) / reps
+        gbmi.set_option(gbmi.OPT_CSR_PATH, 1)       # pair enumeration, forced
         sparse_ms = timed(lambda: gbmi.mi_all_pairs_csr(rp, ci, n, out=out))
         sparse_out = out.clone()
+        gbmi.set_option(gbmi.OPT_CSR_PATH, 0)       # the cost model's choice (default)
+        gbmi.profile(enable=True, reset=True)
+        gbmi.mi_all_pairs_csr(rp, ci, n, out=out)
+        choice = "dense" if "csr_densify" in gbmi.profile(enable=False) else "enumerate"
+        auto_ms = timed(lambda: gbmi.mi_all_pairs_csr(rp, ci, n, out=out))
+        auto_same = bool(torch.equal(out, sparse_out))
         dense_ms = timed(lambda: gbmi.mi_all_pairs(X, out=out, path="fused"))
         rows = torch.arange(0, n, 211, device=dev)
         diff = float((sparse_out[rows] - out[rows]).abs().max())
@@ -589,6 +597,8 @@ def measure_sparse(dev, m=100_000, n=10_000, densities=(0.01, 0.005, 0.001), rep
                                            .sum()),
                     "csr_ms": sparse_ms, "dense_fused_ms": dense_ms,
                     "csr_over_dense_speedup": dense_ms / sparse_ms,
+                    "csr_auto_ms": auto_ms, "csr_auto_form": choice,
+                    "csr_auto_bit_identical": auto_same,
                     "max_abs_diff_sampled_rows": diff})
         del X, rp, ci, sparse_out
         torch.cuda.empty_cache()

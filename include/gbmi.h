@@ -80,12 +80,14 @@ typedef enum {
                                     are 16-byte aligned; bytes must then be 0 / 1 (others are
                                     reported as GBMI_ERR_NOT_BINARY by gbmi_sync).  Saves m*n bytes
                                     of device memory but measured slower (default 0)          */
-    GBMI_OPT_PAIR = 9            /* 1: the single-call and out-of-core tensor-core paths run the
+    GBMI_OPT_PAIR = 9,           /* 1: the single-call and out-of-core tensor-core paths run the
                                     Gram on CTA pairs (clusters of two SMs sharing one tcgen05
                                     cta_group::2 MMA of 256 x 256 x 32; each SM stages half of A
                                     and half of B) whenever that keeps at least as many SMs busy as
                                     single-CTA tiles would; 2: always; 0: single-CTA tiles only
                                     (default 1)                                                  */
+    GBMI_OPT_CSR_PATH = 10       /* CSR input (gbmi_*_csr): 0 = by a cost model (default), 1 = pair
+                                    enumeration, 2 = dense 0/1 matrix + tensor-core path          */
 } gbmi_option;
 
 /* ---------------------------------------------------------------- core calls */
@@ -187,8 +189,11 @@ gbmi_status gbmi_mi_cross_to_host(const uint8_t* X, const uint8_t* Y, int64_t m,
  * ones adds 1 to N11[a][b] for each of its k (k + 1) / 2 pairs a <= b (atomic
  * adds; the diagonal gives the column counts), so the work follows
  * sum_r k_r^2 / 2 instead of m * n^2 / 2: it beats the dense tensor-core path
- * only for very sparse data.  gbmi_mi_all_pairs_csr writes the n x n FP32 MI
- * matrix (out, as mi_all_pairs; values identical to the dense paths);
+ * only for very sparse data.  Elsewhere (by a cost model of the two, from m, n
+ * and nnz; GBMI_OPT_CSR_PATH forces either) the call writes the dense 0/1
+ * matrix into its workspace (m * n bytes) and runs the tensor-core path on it.
+ * gbmi_mi_all_pairs_csr writes the n x n FP32 MI matrix (out, as
+ * mi_all_pairs; values identical to the dense paths, either way);
  * gbmi_counts_all_pairs_csr writes the symmetric n x n int32 counts.  A
  * malformed row (bounds outside [0, nnz], an index outside [0, n), indices not
  * strictly increasing) is skipped and reported as GBMI_ERR_ARG by gbmi_sync.

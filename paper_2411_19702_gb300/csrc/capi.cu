@@ -880,8 +880,25 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
     return st;
 }
 
+// Sparse input: which form is cheaper, by a model of GB300 rates measured on
+// this build (pair enumeration: about 5e10 atomic increments/s, plus the
+// elementwise MI; dense: zero + scatter + pack of m*n bytes at HBM rate, plus
+// the tensor-core Gram at about 3.8e15 flops/s).  The increments are
+// estimated from nnz alone (equal row lengths: sum k(k+1)/2 >= nnz^2/(2m) +
+// nnz/2), so the call stays asynchronous; skewed rows only make the
+// enumeration look cheaper than it is.
+bool csr_dense_is_cheaper(int64_t m, int64_t n, int64_t nnz) {
+    const double dm = static_cast<double>(m), dn = static_cast<double>(n);
+    const double incr = static_cast<double>(nnz) * nnz / (2.0 * dm) + 0.5 * nnz;
+    const double t_enum = incr / 5.0e10 + dn * dn * 8.0 / 6.0e12;
+    const double t_dense = dm * dn * 3.0 / 6.0e12 + dm * dn * dn / 3.8e15;
+    return t_dense < t_enum;
+}
+
 // Sparse input (CSR by samples): pair counts into the upper triangle of N11,
-// then either the symmetric count matrix or the MI of every pair.
+// then either the symmetric count matrix or the MI of every pair; or, when
+// the ones are not sparse enough for that to pay, the dense 0/1 matrix in the
+// workspace and the tensor-core path on it.
 gbmi_status csr_impl(const int64_t* row_ptr, const int32_t* col, int64_t m, int64_t n,
                      int64_t nnz, float* out, int32_t* n11) {
     if (row_ptr == nullptr || (col == nullptr && nnz > 0) || (out == nullptr && n11 == nullptr))
@@ -892,6 +909,18 @@ gbmi_status csr_impl(const int64_t* row_ptr, const int32_t* col, int64_t m, int6
     DeviceCtx* cp = nullptr;
     GBMI_TRY(rt::get_ctx(&cp));
     DeviceCtx& c = *cp;
+    const bool dense = g_opt.csr_path == 2 ||
+                       (g_opt.csr_path == 0 && csr_dense_is_cheaper(m, n, nnz));
+    if (dense) {
+        GBMI_TRY(ensure(c.Xs, static_cast<size_t>(m) * n, "dense input"));
+        uint8_t* Xd = static_cast<uint8_t*>(c.Xs.p);
+        GBMI_CUDA(cudaMemsetAsync(Xd, 0, static_cast<size_t>(m) * n, g_stream), "zero dense input");
+        GBMI_LAUNCH(launch_csr_densify(row_ptr, col, m, n, nnz, Xd,
+                                       static_cast<unsigned int*>(c.err.p), c.sm_count, g_stream),
+                    "csr_densify");
+        if (n11 != nullptr) return counts_impl(Xd, nullptr, m, n, n, n11, GBMI_PATH_AUTO, true);
+        return mi_impl(Xd, nullptr, m, n, n, out, GBMI_PATH_AUTO, true);
+    }
     const size_t cbytes = static_cast<size_t>(n) * n * 4;
     int32_t* N11 = n11;
     if (N11 == nullptr) {
@@ -1088,6 +1117,10 @@ gbmi_status gbmi_set_option(int option, int64_t value) {
         case GBMI_OPT_PAIR:
             if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "pair mode must be 0, 1 or 2");
             g_opt.pair = static_cast<int>(value);
+            return GBMI_OK;
+        case GBMI_OPT_CSR_PATH:
+            if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "CSR path must be 0, 1 or 2");
+            g_opt.csr_path = static_cast<int>(value);
             return GBMI_OK;
         case GBMI_OPT_TILE_N:
             if (value != 0 && value != 64 && value != 128 && value != 256)

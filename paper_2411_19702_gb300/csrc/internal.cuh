@@ -98,6 +98,11 @@ cudaError_t launch_mi_from_counts_sym(const int32_t* N11, int64_t ld_n11, const 
 cudaError_t launch_csr_pair_counts(const int64_t* row_ptr, const int32_t* col, int64_t m,
                                    int64_t n, int64_t nnz, int32_t* N11, unsigned int* err,
                                    int sm_count, cudaStream_t s);
+// Dense uint8 0/1 form of a CSR matrix into X (m x n, zeroed before); a
+// malformed row sets kErrBadCsr and writes nothing.
+cudaError_t launch_csr_densify(const int64_t* row_ptr, const int32_t* col, int64_t m, int64_t n,
+                               int64_t nnz, uint8_t* X, unsigned int* err, int sm_count,
+                               cudaStream_t s);
 cudaError_t launch_diag(const int32_t* N11, int64_t n, int32_t* v, cudaStream_t s);
 cudaError_t launch_mirror_upper(int32_t* N11, int64_t n, cudaStream_t s);
 

@@ -32,6 +32,7 @@ struct Options {
     int tile_n = 0;                      // 0: tuner table / cost model; else forced 64/128/256
     int direct = 0;                      // 1: no pack where X's rows are 16-byte multiples
     int pair = 1;                        // 1: CTA-pair (cta_group::2) Gram where it fills the GPU
+    int csr_path = 0;                    // CSR input: 0 cost model, 1 pair enumeration, 2 dense
 };
 
 struct DeviceCtx {

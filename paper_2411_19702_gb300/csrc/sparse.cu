@@ -10,7 +10,9 @@
 // of N11 with atomic adds.  The kernel checks the CSR structure it reads (row
 // bounds inside [0, nnz], indices inside [0, n) and strictly increasing); a
 // malformed row is skipped and flagged in the error word, so no access leaves
-// the caller's arrays.
+// the caller's arrays.  Where the ones are not that sparse, the C ABI instead
+// writes the dense 0/1 matrix (csr_densify_kernel) and runs the tensor-core
+// path on it.
 #include "internal.cuh"
 
 namespace gbmi {
@@ -64,6 +66,35 @@ csr_pair_counts_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __res
     }
 }
 
+// Dense form of a CSR matrix: X (m x n uint8, zeroed before) gets a 1 at
+// every (sample, variable) listed, one warp per sample, with the same checks
+// as the pair-count kernel (a malformed row writes nothing and is flagged).
+__global__ void __launch_bounds__(kCsrThreads)
+csr_densify_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                   int64_t m, int64_t n, int64_t nnz, uint8_t* X, unsigned int* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * kCsrThreads + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * kCsrThreads) >> 5;
+    for (int64_t r = w0; r < m; r += nw) {
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        if (b < 0 || e < b || e > nnz) {
+            if (lane == 0) atomicOr(err, kErrBadCsr);
+            continue;
+        }
+        const int64_t k = e - b;
+        bool bad = false;
+        for (int64_t q = lane; q < k; q += 32) {
+            const int32_t c = col[b + q];
+            if (c < 0 || c >= n || (q > 0 && col[b + q - 1] >= c)) bad = true;
+        }
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0) atomicOr(err, kErrBadCsr);
+            continue;
+        }
+        for (int64_t q = lane; q < k; q += 32) X[r * n + col[b + q]] = 1;
+    }
+}
+
 // v[j] = N11[j][j] (the diagonal holds each variable's count of ones).
 __global__ void diag_kernel(const int32_t* N11, int64_t n, int32_t* v) {
     for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
@@ -113,6 +144,18 @@ cudaError_t launch_csr_pair_counts(const int64_t* row_ptr, const int32_t* col, i
     const int64_t blocks = (warps * 32 + kCsrThreads - 1) / kCsrThreads;
     csr_pair_counts_kernel<<<static_cast<unsigned>(blocks), kCsrThreads, 0, s>>>(row_ptr, col, m,
                                                                                  n, nnz, N11, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_densify(const int64_t* row_ptr, const int32_t* col, int64_t m, int64_t n,
+                               int64_t nnz, uint8_t* X, unsigned int* err, int sm_count,
+                               cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const int64_t warps_max = static_cast<int64_t>(sm_count > 0 ? sm_count : 152) * 64;
+    const int64_t warps = m < warps_max ? m : warps_max;
+    const int64_t blocks = (warps * 32 + kCsrThreads - 1) / kCsrThreads;
+    csr_densify_kernel<<<static_cast<unsigned>(blocks), kCsrThreads, 0, s>>>(row_ptr, col, m, n,
+                                                                             nnz, X, err);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,14 @@
-"""Sparse input (CSR by samples): pair counts from each sample's ones.
+"""Sparse input (CSR by samples): pair counts from each sample's ones, or the
+dense 0/1 matrix written from the CSR arrays and the tensor-core path.
 
-Counts must be bit-exact against the oracle's direct cell counts; MI within
-1e-6 of the oracle and bit-identical to the dense plain path (same counts,
-same per-pair arithmetic).  Edge cases: empty samples, no ones at all, a
-sample with every variable set, m = 1, n = 1.  Malformed CSR (indices out of
-range or not increasing, row bounds outside the index array) is skipped by
-the kernel's own checks and reported, and the context stays usable.
+Every test runs with both forms forced.  Counts must be bit-exact against the
+oracle's direct cell counts; MI within 1e-6 of the oracle and bit-identical to
+the dense plain path (same counts, same per-pair arithmetic).  Edge cases:
+empty samples, no ones at all, a sample with every variable set, m = 1,
+n = 1.  Malformed CSR (indices out of range or not increasing, row bounds
+outside the index array) is skipped by the kernels' own checks and reported,
+and the context stays usable.  The cost model picks each form where it is
+the cheaper one.
 """
 from __future__ import annotations
 
@@ -18,6 +21,13 @@ import oracle  # noqa: E402
 from paper_2411_19702_gb300 import gbmi  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, params=[1, 2], ids=["enumerate", "densify"])
+def csr_path(request):
+    gbmi.set_option(gbmi.OPT_CSR_PATH, request.param)
+    yield request.param
+    gbmi.set_option(gbmi.OPT_CSR_PATH, 0)
 
 
 def _data(m, n, seed, lo, hi):
@@ -127,3 +137,27 @@ def test_malformed_csr_is_reported(bad):
     gbmi.sync()
     want, _ = oracle.mi_matrix(X)
     assert np.max(np.abs(got.cpu().numpy().astype(np.float64) - want)) <= 1e-6
+
+
+def test_cost_model_choice_and_agreement(csr_path):
+    """Both forms give the same bits; with the model on, a sparse case takes the
+    enumeration and a moderately sparse one the dense path (seen in the launch
+    profile), with the same results."""
+    if csr_path != 1:
+        pytest.skip("runs once")
+    cases = {"sparse": _data(20_000, 3000, 8, 0.0, 0.0004),
+             "moderate": _data(20_000, 3000, 9, 0.005, 0.03)}
+    for name, Xn in cases.items():
+        X = torch.from_numpy(Xn).cuda()
+        rp, ci = gbmi.csr_from_dense(X)
+        outs = {}
+        for mode in (1, 2, 0):
+            gbmi.set_option(gbmi.OPT_CSR_PATH, mode)
+            gbmi.profile(enable=True, reset=True)
+            outs[mode] = gbmi.mi_all_pairs_csr(rp, ci, 3000)
+            gbmi.sync()
+            prof = gbmi.profile(enable=False)
+            if mode == 0:
+                took_dense = "csr_densify" in prof
+                assert took_dense == (name == "moderate"), (name, sorted(prof))
+        assert torch.equal(outs[1], outs[2]) and torch.equal(outs[0], outs[1])
