@@ -449,6 +449,53 @@ def measure_out_of_core(dev, m=100_000, n=50_000, reps=2, seed=6):
     return res
 
 
+# --------------------------------------------------------------- the paper's shapes
+# Table 1 (samples x variables) and the Fig. 2 shape, with the paper's times on its CPU
+# (Opt-T = its PyTorch optimised method; best = its fastest method at that shape).
+PAPER_TABLE = [((1000, 100), 0.021, 0.001), ((100_000, 100), 0.061, 0.013),
+               ((100_000, 1000), 0.086, 0.086), ((100_000, 10_000), 5.6, 5.6)]
+ROW_SWEEP = [(10_000, 1000), (100_000, 1000), (1_000_000, 1000)]       # Fig. 1: rows vary
+COL_SWEEP = [(100_000, 1000), (100_000, 2500), (100_000, 5000), (100_000, 10_000),
+             (100_000, 20_000)]                                          # Fig. 2: columns vary
+
+
+def measure_paper_shapes(dev, reps=5, seed=9):
+    """mi_all_pairs (automatic path) at the paper's benchmark shapes, inputs resident, each
+    with p_j ~ Beta(0.5, 5) columns; the paper's CPU times alongside (context only)."""
+    import torch
+
+    import simdata
+    from paper_2411_19702_gb300 import gbmi
+
+    def time_shape(m, n):
+        X, _ = simdata.make(m, n, seed, "beta", 0.0, 0.05, device=str(dev))
+        out = torch.empty((n, n), dtype=torch.float32, device=dev)
+        gbmi.mi_all_pairs(X, out=out)
+        gbmi.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            gbmi.mi_all_pairs(X, out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        gbmi.sync()
+        ms = e0.elapsed_time(e1) / reps
+        del X, out
+        return ms
+
+    table = []
+    for (m, n), opt_t, best in PAPER_TABLE:
+        ms = time_shape(m, n)
+        table.append({"m": m, "n": n, "ms": ms, "pairs_per_s": n * (n - 1) / 2 / (ms * 1e-3),
+                      "paper_opt_t_s": opt_t, "paper_fastest_s": best,
+                      "vs_paper_opt_t": opt_t / (ms * 1e-3)})
+    rows = [{"m": m, "n": n, "ms": time_shape(m, n)} for m, n in ROW_SWEEP]
+    cols = [{"m": m, "n": n, "ms": time_shape(m, n)} for m, n in COL_SWEEP]
+    torch.cuda.empty_cache()
+    return {"table1_and_fig2": table, "rows_vary_fig1": rows, "columns_vary_fig2": cols,
+            "note": "paper times: Apple M2 CPU (Sec. 4.1), context only"}
+
+
 # --------------------------------------------------------------- cross MI
 def measure_cross(dev, X, reps=5, seed=8, check_pairs=256, use_oracle=True):
     """mi_cross between the workload's X and a second seeded matrix Y of the same shape
@@ -921,6 +968,9 @@ def run_ours(args):
     batch = None
     if not args.skip_batch:
         batch = measure_batch(dev)
+    paper_shapes = None
+    if not args.skip_paper_shapes and rank == 0:
+        paper_shapes = measure_paper_shapes(dev)
     cross = None
     if not args.skip_cross and rank == 0:
         cross = measure_cross(dev, X, use_oracle=not args.skip_oracle)
@@ -982,6 +1032,7 @@ def run_ours(args):
         "out_of_core": out_of_core,
         "sparse": sparse,
         "cross": cross,
+        "paper_shapes": paper_shapes,
         "precision_config": precision,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -1011,6 +1062,7 @@ def main():
     ap.add_argument("--skip-library", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--skip-cross", action="store_true")
+    ap.add_argument("--skip-paper-shapes", action="store_true")
     ap.add_argument("--scaling", choices=["weak", "strong"], default="weak")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()

@@ -86,8 +86,13 @@ typedef enum {
                                     and half of B) whenever that keeps at least as many SMs busy as
                                     single-CTA tiles would; 2: always; 0: single-CTA tiles only
                                     (default 1)                                                  */
-    GBMI_OPT_CSR_PATH = 10       /* CSR input (gbmi_*_csr): 0 = by a cost model (default), 1 = pair
+    GBMI_OPT_CSR_PATH = 10,      /* CSR input (gbmi_*_csr): 0 = by a cost model (default), 1 = pair
                                     enumeration, 2 = dense 0/1 matrix + tensor-core path          */
+    GBMI_OPT_SPLIT_K = 11        /* a single-CTA tensor-core Gram with fewer tiles than SMs (few
+                                    variables, many samples) is split over sample ranges, each
+                                    part's exact int32 counts in its own workspace slice, summed by
+                                    the MI (or counts) kernel: 0 = automatic (default), 1 = never,
+                                    2 = whenever there are samples enough                        */
 } gbmi_option;
 
 /* ---------------------------------------------------------------- core calls */

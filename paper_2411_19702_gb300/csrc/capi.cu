@@ -129,6 +129,126 @@ bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn) {
 // Shard `shard` of `num_shards` runs only that contiguous share of the tile
 // list (the same list and order as the whole problem), so the shards' writes
 // together are the whole result.
+// Sample split of a Gram with too few tiles to fill the GPU (few variables,
+// many samples): the sample range is cut into S parts and every (part, tile)
+// is a unit of one grouped launch (single-CTA or CTA-pair tiles), each part a
+// job writing exact int32 counts into its own slice of the workspace; a final
+// kernel adds the slices and evaluates MI (or writes the counts).  Returns S
+// (1: no split).
+// units: the launch's concurrent tile slots (SMs, or CTA pairs).  S is chosen
+// by a model: the makespan of ceil(S * tiles / units) waves of units 1/S as
+// long, plus the slices' traffic (written by the Gram, read by the final
+// kernel: about 3 x S x n_a x n_b x 4 bytes at HBM rate); a split is taken
+// only when the model gains at least 10% over one part.
+int split_parts(int units, int tiles, int64_t kb_total, int64_t n_a, int64_t n_b) {
+    constexpr int64_t kMinPartKb = 16;     // 2048 samples per part at least
+    constexpr int64_t kMaxParts = 128;
+    constexpr int64_t kMaxSliceBytes = int64_t{2} << 30;
+    constexpr double kBlockSeconds = 0.29e-6;   // one 128-sample K block of one tile unit
+    constexpr double kHbmBytesPerSecond = 6.0e12;
+    const int64_t kb_chunk = kExactChunk / kTcBK;
+    if (g_opt.split_k == 1 || tiles <= 0 || units <= 0) return 1;
+    if (g_opt.split_k != 2 && tiles >= units) return 1;
+    const int64_t exact = (kb_total + kb_chunk - 1) / kb_chunk;   // parts of at most 2^24
+    const double slice = static_cast<double>(n_a) * n_b * 4.0;
+    int64_t s_max = std::min(kMaxParts, kb_total / kMinPartKb);
+    while (s_max > 1 && s_max * slice > kMaxSliceBytes) --s_max;
+    if (s_max < std::max<int64_t>(2, exact)) return 1;
+    const double t_tile = kBlockSeconds * static_cast<double>(kb_total);
+    auto cost = [&](int64_t S) {
+        const int64_t waves = (S * tiles + units - 1) / units;
+        return static_cast<double>(waves) / S * t_tile + 3.0 * S * slice / kHbmBytesPerSecond;
+    };
+    int64_t best = 0;
+    double best_cost = 0.0;
+    for (int64_t S = std::max<int64_t>(2, exact); S <= s_max; ++S) {
+        const double c = cost(S);
+        if (best == 0 || c < best_cost) {
+            best = S;
+            best_cost = c;
+        }
+    }
+    if (best == 0) return 1;
+    if (g_opt.split_k != 2 && exact <= 1 && best_cost > 0.9 * cost(1)) return 1;
+    // equal parts of ceil(kb_total / S) K blocks; drop the parts that would be empty
+    const int64_t kb_s = (kb_total + best - 1) / best;
+    return static_cast<int>((kb_total + kb_s - 1) / kb_s);
+}
+
+gbmi_status run_gram_split(DeviceCtx& c, const OperandMaps& maps, const GramJob& proto, int bn,
+                           bool pair, int tiles, int64_t kb_total, int S, int mode) {
+    const int64_t slice = static_cast<int64_t>(proto.n_a) * proto.n_b;
+    // its own buffer: the caller's counts may live in the workspace's count matrix
+    GBMI_TRY(ensure(c.split_part, static_cast<size_t>(S) * slice * 4, "split partial counts"));
+    int32_t* part = static_cast<int32_t*>(c.split_part.p);
+    const int64_t kb_s = (kb_total + S - 1) / S;   // every part non-empty (split_parts)
+    if ((S - 1) * kb_s >= kb_total || kb_s > kExactChunk / kTcBK)
+        return fail(GBMI_ERR_ARG, "internal: bad sample split");
+    c.split_jobs_host.assign(static_cast<size_t>(S), proto);
+    for (int s = 0; s < S; ++s) {
+        GramJob& j = c.split_jobs_host[static_cast<size_t>(s)];
+        j.bn = bn;
+        j.k_begin = static_cast<int32_t>(s * kb_s);
+        j.k_blocks = static_cast<int32_t>(std::min(kb_s, kb_total - s * kb_s));
+        j.out_f = nullptr;
+        j.out_t = nullptr;
+        j.out_c = part + s * slice;
+        j.ld_out = proto.n_b;
+        j.vec_store = proto.n_b % 4 == 0 ? 1 : 0;
+    }
+    // parts outer, tiles inner: the units in flight share a sample range
+    c.split_tiles_host.resize(static_cast<size_t>(S) * tiles);
+    for (int s = 0; s < S; ++s)
+        for (int t = 0; t < tiles; ++t) {
+            GramTile g = c.tl_host[static_cast<size_t>(t)];
+            g.job = s;
+            c.split_tiles_host[static_cast<size_t>(s) * tiles + t] = g;
+        }
+    GBMI_TRY(ensure(c.split_jobs, c.split_jobs_host.size() * sizeof(GramJob), "split job table"));
+    GBMI_TRY(ensure(c.split_tiles, c.split_tiles_host.size() * sizeof(GramTile), "split tiles"));
+    GBMI_CUDA(cudaMemcpyAsync(c.split_jobs.p, c.split_jobs_host.data(),
+                              c.split_jobs_host.size() * sizeof(GramJob), cudaMemcpyHostToDevice,
+                              g_stream),
+              "split job table upload");
+    GBMI_CUDA(cudaMemcpyAsync(c.split_tiles.p, c.split_tiles_host.data(),
+                              c.split_tiles_host.size() * sizeof(GramTile),
+                              cudaMemcpyHostToDevice, g_stream),
+              "split tile upload");
+    GramLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.jobs = static_cast<const GramJob*>(c.split_jobs.p);
+    L.job0 = c.split_jobs_host[0];
+    L.tiles = static_cast<const GramTile*>(c.split_tiles.p);
+    L.num_tiles = S * tiles;
+    L.pair = pair ? 1 : 0;
+    L.mode = kTcModeCounts;
+    L.err = static_cast<unsigned int*>(c.err.p);
+    L.timeout_ns = g_opt.timeout_ns;
+    L.debug_flags = g_opt.debug_flags;
+    GBMI_TRY(ensure(c.sched, 256, "tile counter"));
+    L.counter = static_cast<unsigned int*>(c.sched.p);
+    GBMI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
+    const int grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, L.num_tiles))
+                          : rt::grid_for(c, L.num_tiles);
+    GBMI_LAUNCH(launch_gram_tc(maps, L, grid, g_stream), "gram_tc_split_counts");
+    if (mode != kTcModeMI) {   // counts: the sum of the slices into the caller's matrix
+        GBMI_LAUNCH(launch_slice_sum(part, proto.n_b, S, slice, proto.n_a, proto.n_b, proto.out_c,
+                                     proto.ld_out, g_stream),
+                    "slice_sum");
+        return GBMI_OK;
+    }
+    if (proto.symmetric)
+        GBMI_LAUNCH(launch_mi_from_counts_sym(part, proto.n_b, proto.va, proto.n_a, proto.mp,
+                                              proto.out_f, proto.ld_out, g_stream, 0, S, slice),
+                    "mi_from_counts");
+    else
+        GBMI_LAUNCH(launch_mi_from_counts(part, proto.n_b, proto.va, proto.vb, proto.n_a,
+                                          proto.n_b, proto.mp, proto.out_f, proto.ld_out,
+                                          g_stream, S, slice),
+                    "mi_from_counts");
+    return GBMI_OK;
+}
+
 gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int64_t m,
                      int mode, const OperandMaps* dmaps = nullptr, int shard = 0,
                      int num_shards = 1) {
@@ -140,10 +260,17 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     // CTA pairs: 256 x 256 tiles on clusters of two SMs (packed operands only)
     const bool pair = dmaps == nullptr &&
                       use_pair(c, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn);
+    const int64_t kb_all = pack_ld(m) / kTcBK;
     const int bn = pair ? kTcBNMax : proto.bn;
     const int bm = pair ? 2 * kTcBM : kTcBM;
     int tiles = 0;
     GBMI_TRY(tile_list(c, proto.n_a, proto.n_b, proto.symmetric != 0, bn, &tiles, bm));
+    if (dmaps == nullptr && num_shards == 1 && proto.out_t == nullptr &&
+        (mode == kTcModeMI || mode == kTcModeCounts)) {
+        const int S = split_parts(pair ? c.pair_clusters : c.sm_count, tiles, kb_all,
+                                  proto.n_a, proto.n_b);
+        if (S > 1) return run_gram_split(c, maps, proto, bn, pair, tiles, kb_all, S, mode);
+    }
     GramLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.jobs = nullptr;
@@ -1118,6 +1245,10 @@ gbmi_status gbmi_set_option(int option, int64_t value) {
             if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "pair mode must be 0, 1 or 2");
             g_opt.pair = static_cast<int>(value);
             return GBMI_OK;
+        case GBMI_OPT_SPLIT_K:
+            if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "split mode must be 0, 1 or 2");
+            g_opt.split_k = static_cast<int>(value);
+            return GBMI_OK;
         case GBMI_OPT_CSR_PATH:
             if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "CSR path must be 0, 1 or 2");
             g_opt.csr_path = static_cast<int>(value);
@@ -1182,6 +1313,9 @@ gbmi_status gbmi_shutdown(void) {
         cudaSetDevice(d);
         cudaDeviceSynchronize();
         rt::release(c->sched);
+        rt::release(c->split_jobs);
+        rt::release(c->split_tiles);
+        rt::release(c->split_part);
         for (DevBuf* b : {&c->P, &c->Ba, &c->Bb, &c->va, &c->vb, &c->ha, &c->hb, &c->counts,
                           &c->T, &c->err, &c->tiles, &c->Xs, &c->Ys, &c->outs, &c->flag,
                           &c->panel})

@@ -44,17 +44,37 @@ __global__ void mi_vars_grouped_kernel(const int32_t* v, const int64_t* var_begi
     }
 }
 
+// Count at index idx of `slices` partial count matrices stride elements apart
+// (the sample ranges of a split Gram); exact int32 sums.
+__device__ __forceinline__ int32_t slice_sum(const int32_t* N11, int64_t idx, int slices,
+                                             int64_t stride) {
+    int32_t v = N11[idx];
+    for (int k = 1; k < slices; ++k) v += N11[idx + k * stride];
+    return v;
+}
+
 // One thread per output element; a CTA covers 256 consecutive j of one row
 // block, so N11 reads and MI writes are coalesced and the row terms uniform.
 __global__ void mi_from_counts_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* va,
                                       const MiVar* vb, int64_t n1, int64_t n2, const MiParams P,
-                                      float* out, int64_t ld_out) {
+                                      float* out, int64_t ld_out, int slices, int64_t stride) {
     const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (j >= n2) return;
     const MiVar B = load_var(vb + j);
     for (int64_t i = blockIdx.y; i < n1; i += gridDim.y) {
         const MiVar A = load_var(va + i);
-        out[i * ld_out + j] = mi_pair(N11[i * ld_n11 + j], A, B, P);
+        out[i * ld_out + j] = mi_pair(slice_sum(N11, i * ld_n11 + j, slices, stride), A, B, P);
+    }
+}
+
+// out[i][j] = sum over the slices of N11[i][j] (rows x cols, both row-major).
+__global__ void slice_sum_kernel(const int32_t* N11, int64_t ld_n11, int slices, int64_t stride,
+                                 int64_t rows, int64_t cols, int32_t* out, int64_t ld_out) {
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = e / cols, j = e % cols;
+        out[i * ld_out + j] = slice_sum(N11, i * ld_n11 + j, slices, stride);
     }
 }
 
@@ -67,7 +87,7 @@ constexpr int kSymTile = 32;
 __global__ void __launch_bounds__(256)
 mi_from_counts_sym_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* vars, int64_t n,
                           const MiParams P, float* out, int64_t ld_out, int64_t tiles_per_side,
-                          int upper_only) {
+                          int upper_only, int slices, int64_t stride) {
     __shared__ float T[kSymTile][kSymTile + 1];
     // tile index -> (I, J) with I <= J, row-major over the upper triangle
     // first tile of row I: S(I) = I * tps - I (I - 1) / 2; take the largest I
@@ -93,7 +113,7 @@ mi_from_counts_sym_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* vars,
             const MiVar A = load_var(vars + i);
             // upper_only: only N11[a][b], a <= b, is filled
             const int64_t lo = (upper_only && i > j) ? j : i, hi = (upper_only && i > j) ? i : j;
-            v = mi_pair(N11[lo * ld_n11 + hi], A, B, P);
+            v = mi_pair(slice_sum(N11, lo * ld_n11 + hi, slices, stride), A, B, P);
             out[i * ld_out + j] = v;
         }
         T[r][tx] = v;
@@ -113,13 +133,26 @@ mi_from_counts_sym_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* vars,
 
 cudaError_t launch_mi_from_counts_sym(const int32_t* N11, int64_t ld_n11, const MiVar* vars,
                                       int64_t n, const MiParams& P, float* out, int64_t ld_out,
-                                      cudaStream_t s, int upper_only) {
+                                      cudaStream_t s, int upper_only, int slices,
+                                      int64_t slice_stride) {
     if (n <= 0) return cudaSuccess;
+    if (slices < 1) return cudaErrorInvalidValue;
     const int64_t tps = (n + kSymTile - 1) / kSymTile;
     const int64_t tiles = tps * (tps + 1) / 2;
     if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
     mi_from_counts_sym_kernel<<<static_cast<unsigned>(tiles), 256, 0, s>>>(
-        N11, ld_n11, vars, n, P, out, ld_out, tps, upper_only);
+        N11, ld_n11, vars, n, P, out, ld_out, tps, upper_only, slices, slice_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_sum(const int32_t* N11, int64_t ld_n11, int slices, int64_t slice_stride,
+                             int64_t rows, int64_t cols, int32_t* out, int64_t ld_out,
+                             cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (slices < 1) return cudaErrorInvalidValue;
+    const int64_t blocks = (rows * cols + 255) / 256;
+    slice_sum_kernel<<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(
+        N11, ld_n11, slices, slice_stride, rows, cols, out, ld_out);
     return cudaGetLastError();
 }
 
@@ -155,12 +188,15 @@ cudaError_t launch_mi_vars_grouped(const int32_t* v, const int64_t* var_begin, i
 
 cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const MiVar* va,
                                   const MiVar* vb, int64_t n1, int64_t n2, const MiParams& P,
-                                  float* out, int64_t ld_out, cudaStream_t s) {
+                                  float* out, int64_t ld_out, cudaStream_t s, int slices,
+                                  int64_t slice_stride) {
+    if (slices < 1) return cudaErrorInvalidValue;
     const int64_t bx = (n2 + 255) / 256;
     if (bx > 0x7FFFFFFF) return cudaErrorInvalidValue;
     const int64_t by = n1 < 65535 ? n1 : 65535;
     dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
-    mi_from_counts_kernel<<<grid, 256, 0, s>>>(N11, ld_n11, va, vb, n1, n2, P, out, ld_out);
+    mi_from_counts_kernel<<<grid, 256, 0, s>>>(N11, ld_n11, va, vb, n1, n2, P, out, ld_out,
+                                               slices, slice_stride);
     return cudaGetLastError();
 }
 

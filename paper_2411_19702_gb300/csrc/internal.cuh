@@ -83,14 +83,23 @@ cudaError_t launch_mi_vars(const int32_t* v, int64_t n, const MiParams& P, MiVar
 cudaError_t launch_mi_vars_grouped(const int32_t* v, const int64_t* var_begin, int njobs,
                                    int64_t total, const MiParams* params, MiVar* out,
                                    cudaStream_t s);
+// MI from counts.  slices > 1: the counts are the sums of `slices` partial
+// count matrices slice_stride elements apart (the sample ranges of a split
+// Gram), added exactly in int32.
 cudaError_t launch_mi_from_counts(const int32_t* N11, int64_t ld_n11, const MiVar* va,
                                   const MiVar* vb, int64_t n1, int64_t n2, const MiParams& P,
-                                  float* out, int64_t ld_out, cudaStream_t s);
+                                  float* out, int64_t ld_out, cudaStream_t s, int slices = 1,
+                                  int64_t slice_stride = 0);
 // All pairs of one matrix (N11 symmetric): each unordered pair evaluated once,
 // written to (i, j) and (j, i).  upper_only: only N11[a][b], a <= b, is read.
 cudaError_t launch_mi_from_counts_sym(const int32_t* N11, int64_t ld_n11, const MiVar* vars,
                                       int64_t n, const MiParams& P, float* out, int64_t ld_out,
-                                      cudaStream_t s, int upper_only = 0);
+                                      cudaStream_t s, int upper_only = 0, int slices = 1,
+                                      int64_t slice_stride = 0);
+// out (rows x cols) = the sum of `slices` partial count matrices.
+cudaError_t launch_slice_sum(const int32_t* N11, int64_t ld_n11, int slices, int64_t slice_stride,
+                             int64_t rows, int64_t cols, int32_t* out, int64_t ld_out,
+                             cudaStream_t s);
 
 // ------------------------------------------------------------ sparse input
 // Upper triangle (with the diagonal) of N11 from X in CSR by samples (N11

@@ -33,6 +33,7 @@ struct Options {
     int direct = 0;                      // 1: no pack where X's rows are 16-byte multiples
     int pair = 1;                        // 1: CTA-pair (cta_group::2) Gram where it fills the GPU
     int csr_path = 0;                    // CSR input: 0 cost model, 1 pair enumeration, 2 dense
+    int split_k = 0;                     // sample split of few-tile Grams: 0 auto, 1 off, 2 forced
 };
 
 struct DeviceCtx {
@@ -40,6 +41,11 @@ struct DeviceCtx {
     int sm_count = 0;
     DevBuf P, Ba, Bb, va, vb, ha, hb, counts, T, err, tiles, Xs, Ys, outs, flag;
     DevBuf sched;   // tile counter of the Gram launches (zeroed before each launch)
+    // split Gram (sample ranges as jobs): job table and tile list, host copies kept
+    // alive for the asynchronous uploads
+    DevBuf split_jobs, split_tiles, split_part;   // split_part: the parts' count slices
+    std::vector<GramJob> split_jobs_host;
+    std::vector<GramTile> split_tiles_host;
     int64_t T_len = 0;
     // tile-list cache of the single-dataset path
     int64_t tl_na = -1, tl_nb = -1;
