@@ -12,9 +12,11 @@
 //
 // A CTA owns 128 variables and a run of 128-sample tiles.  Each tile is read
 // with coalesced 16-byte loads (the next tile's loads are in flight while the
-// current one is transposed), transposed through shared memory in 4x4 byte
-// blocks with byte permutes, and written out so that every warp store covers
-// whole 128-byte rows of P (a tile's output is one contiguous 16 KB block).
+// current one is transposed; rows that are not 16-byte aligned are copied by
+// cp.async as aligned granules and realigned from shared memory), transposed
+// through shared memory in 4x4 byte blocks with byte permutes, and written
+// out so that every warp store covers whole 128-byte rows of P (a tile's
+// output is one contiguous 16 KB block).
 // A grouped launch covers many datasets: CTA c works for the job whose CTA
 // range holds c.
 #include "internal.cuh"
@@ -53,29 +55,26 @@ __device__ __forceinline__ void transpose4x4(const uint32_t w0, const uint32_t w
     c3 = __byte_perm(t2, t3, 0x7632);
 }
 
-// Bytes [s, s + 16) of the 32 bytes g0:g1 (two consecutive aligned 16-byte
-// granules), of which the first keep (<= 16) are kept and the rest zeroed.
-__device__ __forceinline__ uint4 realign16(const uint4 g0, const uint4 g1, int s, int keep) {
-    const uint32_t w[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-    const int q = s >> 2;
-    const uint32_t sh = static_cast<uint32_t>(s & 3) * 8u;
-    uint32_t sel[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-        sel[i] = q == 0 ? w[i] : (q == 1 ? w[i + 1] : (q == 2 ? w[i + 2] : w[i + 3]));
-    uint32_t o[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        o[i] = __funnelshift_r(sel[i], sel[i + 1], sh);
-        const int k = keep - 4 * i;   // bytes of this word that are valid
-        if (k <= 0) {
-            o[i] = 0u;
-        } else if (k < 4) {
-            o[i] &= (1u << (8 * k)) - 1u;
-        }
-    }
-    return make_uint4(o[0], o[1], o[2], o[3]);
+// Asynchronous 16-byte copy global -> shared of the first `bytes` (0..16) bytes
+// of a 16-byte aligned granule; the rest of the destination is zero-filled and
+// no byte past `bytes` is read.
+__device__ __forceinline__ void cp_async16(uint32_t dst_smem, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst_smem), "l"(src),
+                 "r"(bytes)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Unaligned rows: every warp stages its 16 rows of a tile (4 per quarter) as
+// the 9 aligned 16-byte granules that cover each row's 128-byte slice (row
+// stride 144 bytes).
+constexpr int kRawRowBytes = 144;
+constexpr int kRawWarpBytes = 16 * kRawRowBytes;
 
 // Low bits of the four 0/1 bytes of x, packed into a nibble (byte k -> bit k).
 __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
@@ -91,7 +90,7 @@ __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
 // and the column-wise reads of the transpose free of bank conflicts.
 template <bool kAligned>
 __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, const int64_t by,
-                                         uint8_t* S) {
+                                         uint8_t* S, uint8_t* raw) {
     const int t = threadIdx.x;
     const int w = t >> 5;
     const int lane = t & 31;
@@ -109,20 +108,23 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
 
     // The next tile's loads are issued before the current tile is transposed
     // and stored, so they are in flight during that work.  Aligned rows: one
-    // 16-byte load per lane and row.  Rows of X that are not 16-byte aligned:
-    // the (at most two) aligned granules that hold each lane's 16 bytes,
-    // realigned only when the tile is written to shared memory; only granules
-    // holding bytes of [j, min(j + 16, n)) are read.
-    // The next tile's loads are issued before the current tile is transposed
-    // and stored, so they are in flight during that work.  Unaligned rows:
-    // each lane reads the (at most two) aligned granules holding its 16 bytes,
-    // all eight loads first, then realigns them (funnel shifts); only granules
-    // holding bytes of [j, min(j + 16, n)) are read.
+    // 16-byte load per lane and row, into registers.  Rows of X that are not
+    // 16-byte aligned: the aligned granules covering each row's 128-byte slice
+    // (lane l of the row's 8 lanes copies granule l, lane 7 also granule 8)
+    // go to this warp's raw rows in shared memory by cp.async, copying only
+    // bytes of [j0, min(j0 + 128, n)) of the row and zero-filling the rest; the
+    // realignment (5 word reads and 4 funnel shifts per lane and row) happens
+    // when the tile is written to S, so no registers hold the loads meanwhile.
     uint4 pre[4];
+    // unaligned rows: this warp's raw rows, the lane's row among the warp's 4 per
+    // quarter, and its granule
+    auto wraw = [&] { return raw + (t >> 5) * kRawWarpBytes; };
+    const int rr_w = (t >> 3) & 3;
+    const int gl = t & 7;
     auto issue_tile = [&](int64_t tile) {
         const int64_t r0 = tile * kTileR;
-        const int64_t jl = j0 + (t & 7) * 16;
         if constexpr (kAligned) {
+            const int64_t jl = j0 + (t & 7) * 16;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int64_t r = r0 + q * 32 + (t >> 3);
@@ -131,35 +133,58 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
                     pre[q] = __ldg(reinterpret_cast<const uint4*>(a.X + r * a.ldx + jl));
             }
         } else {
-            const int keep_j =
-                jl >= a.n ? 0 : (a.n - jl < 16 ? static_cast<int>(a.n - jl) : 16);
-            uint4 g1[4];
-            uint32_t meta = 0;   // row q: misalignment in bits 8q..8q+3, valid in bit 8q+4
+            const int64_t keep_row = a.n - j0 < kTileJ ? a.n - j0 : kTileJ;   // >= 1
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int64_t r = r0 + q * 32 + (t >> 3);
-                pre[q] = g1[q] = make_uint4(0, 0, 0, 0);
-                if (r < a.m && keep_j > 0) {
-                    const uintptr_t ad = reinterpret_cast<uintptr_t>(a.X + r * a.ldx + jl);
-                    const int s = static_cast<int>(ad & 15);
-                    meta |= static_cast<uint32_t>(s | 16) << (8 * q);
-                    const uint4* g = reinterpret_cast<const uint4*>(ad - s);
-                    pre[q] = __ldg(g);
-                    if (s + keep_j > 16) g1[q] = __ldg(g + 1);
+                const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(
+                    wraw() + (4 * q + rr_w) * kRawRowBytes + 16 * gl));
+                if (r < a.m) {
+                    const uintptr_t ad = reinterpret_cast<uintptr_t>(a.X + r * a.ldx + j0);
+                    const int sft = static_cast<int>(ad & 15);
+                    const uint8_t* G = reinterpret_cast<const uint8_t*>(ad - sft);
+                    // valid bytes of granule k: [sft, sft + keep_row) in the row's granules
+                    const int64_t end = sft + keep_row;
+                    const int64_t n0 = end - 16 * gl;
+                    cp_async16(dst, G + 16 * gl,
+                               static_cast<uint32_t>(n0 <= 0 ? 0 : (n0 > 16 ? 16 : n0)));
+                    if (gl == 7) {
+                        const int64_t n8 = end - 128;
+                        cp_async16(dst + 16, G + 128,
+                                   static_cast<uint32_t>(n8 <= 0 ? 0 : (n8 > 16 ? 16 : n8)));
+                    }
+                } else {   // samples beyond m: zeros
+                    cp_async16(dst, a.X, 0u);
+                    if (gl == 7) cp_async16(dst + 16, a.X, 0u);
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t mq = (meta >> (8 * q)) & 0x1Fu;
-                pre[q] = realign16(pre[q], g1[q], static_cast<int>(mq & 15u),
-                                   mq & 16u ? keep_j : 0);
-            }
+            cp_async_commit();
         }
     };
     if (tile_begin < tile_end) issue_tile(tile_begin);
 
     for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
         const int64_t r0 = tile * kTileR;
+        if constexpr (!kAligned) {
+            // this tile's raw rows have landed (the warp's own copies) -> realign
+            cp_async_wait_all();
+            __syncwarp();
+            const uint32_t* wr = reinterpret_cast<const uint32_t*>(wraw());
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t r = r0 + q * 32 + (t >> 3);
+                const int sft = r < a.m ? static_cast<int>(reinterpret_cast<uintptr_t>(
+                                                               a.X + r * a.ldx + j0) & 15)
+                                        : 0;
+                const uint32_t* row = wr + (4 * q + rr_w) * (kRawRowBytes / 4) + (sft >> 2) +
+                                      4 * gl;
+                const uint32_t sh = static_cast<uint32_t>(sft & 3) * 8u;
+                const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3], w4 = row[4];
+                pre[q] = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                                    __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+            }
+            __syncwarp();   // the raw rows are refilled by the next issue
+        }
         // ---- 128 samples x 128 variables into S (row r, swizzled 16-byte chunks)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -232,14 +257,16 @@ template <bool kAligned>
 __global__ void __launch_bounds__(kPackThreads, 4)   // 4 CTAs per SM: loads in flight
 pack_kernel(const PackJob job) {
     __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
+    __shared__ __align__(16) uint8_t R[kAligned ? 16 : (kPackThreads / 32) * kRawWarpBytes];
     const int64_t c = blockIdx.x;
-    pack_cta<kAligned>(job, c % job.gx, c / job.gx, S);
+    pack_cta<kAligned>(job, c % job.gx, c / job.gx, S, R);
 }
 
 __global__ void __launch_bounds__(kPackThreads, 4)
 pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs,
                     const int32_t* __restrict__ cta_job) {
     __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
+    __shared__ __align__(16) uint8_t R[(kPackThreads / 32) * kRawWarpBytes];
     const int64_t c = blockIdx.x;
     int lo = 0, hi = njobs - 1;   // last job whose cta_begin <= c
     if (cta_job != nullptr) {
@@ -253,9 +280,9 @@ pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs,
     const PackJob job = jobs[lo];
     const int64_t cl = c - job.cta_begin;
     if (job.vec)
-        pack_cta<true>(job, cl % job.gx, cl / job.gx, S);
+        pack_cta<true>(job, cl % job.gx, cl / job.gx, S, R);
     else
-        pack_cta<false>(job, cl % job.gx, cl / job.gx, S);
+        pack_cta<false>(job, cl % job.gx, cl / job.gx, S, R);
 }
 
 __global__ void validate_kernel(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
