@@ -64,7 +64,6 @@ void set_pack_pointers(PackJob& pj, const uint8_t* X) {
 
 void set_gram_output(GramJob& g, float* out) {
     g.out_f = out;
-    g.vec_store = (g.ld_out % 4 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
 }
 
 gbmi_status upload(rt::DevBuf& b, const void* host, size_t bytes, const char* what) {

@@ -194,7 +194,6 @@ gbmi_status run_gram_split(DeviceCtx& c, const OperandMaps& maps, const GramJob&
         j.out_t = nullptr;
         j.out_c = part + s * slice;
         j.ld_out = proto.n_b;
-        j.vec_store = proto.n_b % 4 == 0 ? 1 : 0;
     }
     // parts outer, tiles inner: the units in flight share a sample range
     c.split_tiles_host.resize(static_cast<size_t>(S) * tiles);
@@ -401,9 +400,6 @@ GramJob tc_job(const TcLayout& L, int64_t m, int64_t n1, int64_t n2, bool sym, i
     g.n_b = static_cast<int32_t>(n2);
     g.symmetric = sym ? 1 : 0;
     g.bn = bn;
-    const uintptr_t base = reinterpret_cast<uintptr_t>(out_f ? static_cast<void*>(out_f)
-                                                             : static_cast<void*>(out_c));
-    g.vec_store = (n2 % 4 == 0 && base % 16 == 0) ? 1 : 0;
     g.va = va;
     g.vb = vb;
     g.out_f = out_f;
@@ -744,7 +740,6 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
         G.job0.vb = vb;
         G.job0.out_f = static_cast<float*>(c.outs.p);
         G.job0.out_c = gchunks > 1 ? counts : nullptr;
-        G.job0.vec_store = (n2 % 4 == 0) ? 1 : 0;
         G.panel_done = counters;
         G.panel_target = targets;
         G.host_flags = c.dflags;
@@ -893,7 +888,6 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
             g.bn = kTcBNMax;
             pair_panel[static_cast<size_t>(p)] = 1;
         }
-        g.vec_store = (w % 4 == 0) ? 1 : 0;
         g.va = va + i0;
         g.vb = vb + j0;
         g.ld_out = w;

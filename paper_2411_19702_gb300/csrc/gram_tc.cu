@@ -482,7 +482,6 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             float* const out_f = job.out_f;
             float* const out_t = job.out_t;
             const int64_t ld_out = job.ld_out, ld_t = job.ld_t;
-            const bool vec_store = job.vec_store != 0;
             // counts of earlier sample chunks (or null): n11 = prefix + this launch's
             const int32_t* const prefix = job.out_c;
             uint32_t cur[4];
@@ -518,9 +517,18 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                         if (sym && j < n_b && j > i) out_f[j * ld_out + i] = v[q];
                         if (out_t != nullptr && j < n_b) out_t[j * ld_t + i] = v[q];
                     }
-                    if (j0 + 4 <= n_b && (!sym || j0 >= i) && vec_store) {
-                        *reinterpret_cast<float4*>(out_f + i * ld_out + j0) =
-                            make_float4(v[0], v[1], v[2], v[3]);
+                    // (i, j): one 16-byte vector, or two 8-byte ones, as the row's
+                    // alignment allows (rows of an odd-width output differ)
+                    float* const rowp = out_f + i * ld_out + j0;
+                    const uint32_t al =
+                        static_cast<uint32_t>(reinterpret_cast<uintptr_t>(rowp)) & 15u;
+                    if (j0 + 4 <= n_b && (!sym || j0 >= i) && (al & 7u) == 0) {
+                        if (al == 0) {
+                            *reinterpret_cast<float4*>(rowp) = make_float4(v[0], v[1], v[2], v[3]);
+                        } else {
+                            reinterpret_cast<float2*>(rowp)[0] = make_float2(v[0], v[1]);
+                            reinterpret_cast<float2*>(rowp)[1] = make_float2(v[2], v[3]);
+                        }
                     } else {
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
@@ -627,7 +635,10 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             // (i, j): 16 consecutive columns of this thread's row
             if (!row_ok) continue;
             const bool full = (j0 + kGroup <= n_b) && (!sym || j0 >= i);
-            if (full && job.vec_store) {
+            const uintptr_t rowp = is_mi<kMode>()
+                                       ? reinterpret_cast<uintptr_t>(job.out_f + i * job.ld_out + j0)
+                                       : reinterpret_cast<uintptr_t>(job.out_c + i * job.ld_out + j0);
+            if (full && (rowp & 15u) == 0) {
                 if (is_mi<kMode>()) {
                     float4* dst = reinterpret_cast<float4*>(job.out_f + i * job.ld_out + j0);
 #pragma unroll

@@ -147,7 +147,6 @@ struct GramJob {
     int32_t n_a, n_b;          // valid variables of A and B
     int32_t symmetric;         // A == B: write (i, j) and (j, i) for j >= i only
     int32_t bn;                // B rows per tile: 64, 128 or 256
-    int32_t vec_store;         // output rows are 16-byte aligned
     int32_t pad;
     const MiVar* va;           // per-variable terms (MI mode)
     const MiVar* vb;

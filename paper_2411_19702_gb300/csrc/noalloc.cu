@@ -185,7 +185,6 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     g.n_b = static_cast<int32_t>(n);
     g.symmetric = 1;
     g.bn = kTileN;
-    g.vec_store = (n % 4 == 0 && oa % 16 == 0) ? 1 : 0;
     g.va = vars;
     g.vb = vars;
     g.out_f = out;

@@ -262,7 +262,6 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
             std::lock_guard<std::recursive_mutex> lk(rt::g_mu);
             g.bn = rt::choose_bn(r.m, r.n_a, r.n_b, sym);
         }
-        g.vec_store = (r.n_b % 4 == 0) ? 1 : 0;   // outputs are 256-byte aligned in the arena
         g.va = vars_of(S, da);
         g.vb = vars_of(S, db);
         g.out_f = reinterpret_cast<float*>(at(S, r.off_out));
