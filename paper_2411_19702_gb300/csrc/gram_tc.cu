@@ -146,6 +146,16 @@ __device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
     return L.jobs != nullptr ? L.jobs[j] : L.job0;
 }
 
+// MMA width of a tile: the job's tile width, or, for the ragged last column
+// block, its valid columns rounded up to 32 (a valid N for M = 128 on one CTA
+// and M = 256 on a pair); the columns beyond are masked by every epilogue.
+__device__ __forceinline__ int tile_n(const GramJob& job, const GramTile& tile) {
+    const int64_t w = static_cast<int64_t>(job.n_b) - static_cast<int64_t>(tile.J) * job.bn;
+    if (w >= job.bn) return job.bn;
+    const int n = static_cast<int>((w + 31) / 32 * 32);
+    return n < 32 ? 32 : n;
+}
+
 // ------------------------------------------------------------------ producer
 // Next tile of this CTA: from the shared counter (dynamic order) or the static
 // round-robin sequence.
@@ -206,6 +216,8 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         const uint32_t bytes = static_cast<uint32_t>((Plan<kPair>::tile_m + bn) * kTcBK);
         const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m;
         const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn;
+        // pair: the partner CTA holds B rows [N/2, N) of the tile's MMA width N
+        const int nhalf = kPair ? tile_n(job, tile) / 2 : 0;
         if (L.direct && ((a0 | b0) & 15) != 0) {
             // a direct copy's x coordinate (a variable index) must be a multiple
             // of 16 bytes: record it and issue nothing
@@ -232,7 +244,7 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
                 ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.a(stage)), 1u),
                                       &maps.box128, sm.full(stage), 0, ya + kTcBM);
                 ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.b(stage)), 1u),
-                                      &maps.box128, sm.full(stage), 0, yb + kTcBM);
+                                      &maps.box128, sm.full(stage), 0, yb + nhalf);
             } else if (L.direct) {
                 // 128 variables x 128 samples of X per box; B in bn / 128 boxes
                 const int32_t y = static_cast<int32_t>(k * kTcBK);
@@ -298,9 +310,9 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
         const uint32_t idesc =
-            kPair ? ptx::idesc_e4m3_f32(2 * kTcBM, static_cast<uint32_t>(job.bn))
+            kPair ? ptx::idesc_e4m3_f32(2 * kTcBM, static_cast<uint32_t>(tile_n(job, tile)))
             : L.direct ? ptx::idesc_e4m3_f32_mnmajor(kTcBM, static_cast<uint32_t>(job.bn))
-                       : ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(job.bn));
+                       : ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(tile_n(job, tile)));
         const int k_blocks = job.k_blocks;
         if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, L.timeout_ns,
                                     sm.abort_flag())) {
