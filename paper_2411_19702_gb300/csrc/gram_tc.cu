@@ -15,23 +15,30 @@
 // the operands' first rows in the shared buffer, its sample range, its tile
 // width bn (64, 128 or 256), its epilogue terms and its output.
 //
-// Persistent, warp-specialised CTA (320 threads, one CTA per SM):
+// Persistent, warp-specialised CTA, one per SM (576 threads; 320 for the
+// variant with the FP64 combine), or CTA pairs (clusters of 2, kPair):
 //   warp 0      TMA producer: per stage one 128 x 128-byte box of A (the
 //               variables of row block I) and one bn x 128-byte box of B
 //               (column block J) into a 4-stage shared-memory ring
-//               (128-byte swizzle).
+//               (128-byte swizzle).  In a pair, CTA 0's producer loads both
+//               CTAs' halves (128 rows of A and of B each) into a 6-stage
+//               ring, the partner's through the cluster window.
 //   warp 1      allocates 512 TMEM columns; one thread issues
-//               tcgen05.mma.kind::f8f6f4 M=128 N=bn K=32 (4 per stage) into
-//               one of two 256-column FP32 accumulators, commits each stage
-//               back to the ring and each finished tile to the epilogue.
-//   warps 2-9   epilogue, two warps per TMEM lane quadrant (tcgen05.ld only
-//               reaches lanes 32*(warp%4)..+31), each taking bn/2 columns:
-//               load 16 accumulator columns at a time (one TMEM lane = one
-//               variable i per thread), derive n10, n01, n00, evaluate MI and
-//               store (i, j) as 16-byte vectors and, for a symmetric problem,
-//               (j, i) as coalesced rows (or, for a panel of an out-of-core
-//               run, (j, i) into a separate mirror buffer).  The second
-//               accumulator lets tile t+1's MMAs run meanwhile.
+//               tcgen05.mma.kind::f8f6f4 M=128 N=bn K=32 (4 per stage; in a
+//               pair, CTA 0 issues cta_group::2 M=256 N=256) into one of two
+//               256-column FP32 accumulators, commits each stage back to the
+//               ring and each finished tile to the epilogue.  The ragged last
+//               column block runs at its valid width rounded up to 32.
+//   warps 2-17  epilogue (warps 2-9 for the FP64-combine variant), four (two)
+//               warps per TMEM lane quadrant (tcgen05.ld only reaches lanes
+//               32*(warp%4)..+31), each taking a quarter (half) of the tile's
+//               columns: load accumulator columns (one TMEM lane = one variable
+//               i per thread), derive n10, n01, n00, evaluate MI and store
+//               (i, j) as 16-, 8- or 4-byte pieces as the row's alignment
+//               allows and, for a symmetric problem, (j, i) as coalesced rows
+//               (or, for a panel of an out-of-core run, (j, i) into a separate
+//               mirror buffer).  The second accumulator lets tile t+1's MMAs
+//               run meanwhile.
 // Tiles come from a host-built list: for all-pairs only blocks that touch
 // the upper triangle (j >= i), in groups of column blocks, jobs one after
 // another, so that CTAs running at the same time share operand panels in L2.
