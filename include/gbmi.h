@@ -50,20 +50,21 @@ typedef enum {
 } gbmi_status;
 
 /* Computation paths.  AUTO picks the fused tensor-core path, or the popcount
- * path for tiny shapes.  The tensor-core Gram counts exactly in FP32 up to
+ * path for tiny shapes.  The tensor-core Gram multiplies 0/1 operands packed
+ * as FP4 E2M1 (GBMI_OPT_FP4, the default) or FP8 E4M3 and counts exactly in FP32 up to
  * 2^24 samples per launch; beyond that it runs in sample chunks of 2^24,
  * accumulating int32 counts in its workspace (n1 * n2 * 4 bytes), and the
  * fused path evaluates MI in the last chunk's epilogue. */
 typedef enum {
     GBMI_PATH_AUTO = 0,
-    GBMI_PATH_FUSED = 1,     /* tcgen05 FP8 Gram with the MI epilogue fused (one pass)      */
-    GBMI_PATH_PLAIN = 2,     /* tcgen05 FP8 Gram -> int32 N11 in HBM, then elementwise MI   */
+    GBMI_PATH_FUSED = 1,     /* tcgen05 FP4/FP8 Gram with the MI epilogue fused (one pass)  */
+    GBMI_PATH_PLAIN = 2,     /* tcgen05 FP4/FP8 Gram -> int32 N11 in HBM, then elementwise MI */
     GBMI_PATH_POPCOUNT = 3   /* bit-packed AND + popcount Gram (exactness cross-check)      */
 } gbmi_path;
 
 /* Options for gbmi_set_option.  Their defaults can also be set in the
  * environment when the library loads: GBMI_FIXUP, GBMI_TILE_N, GBMI_PAIR,
- * GBMI_DIRECT, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS (out-of-range
+ * GBMI_DIRECT, GBMI_FP4, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS (out-of-range
  * values are ignored).  GBMI_LOG=1 also writes every error text to stderr. */
 typedef enum {
     GBMI_OPT_FIXUP = 1,          /* 1: FP64 n*log2(n) combine for pairs whose FP32 MI < 1e-4 (default 0) */
@@ -88,11 +89,19 @@ typedef enum {
                                     (default 1)                                                  */
     GBMI_OPT_CSR_PATH = 10,      /* CSR input (gbmi_*_csr): 0 = by a cost model (default), 1 = pair
                                     enumeration, 2 = dense 0/1 matrix + tensor-core path          */
-    GBMI_OPT_SPLIT_K = 11        /* a single-CTA tensor-core Gram with fewer tiles than SMs (few
+    GBMI_OPT_SPLIT_K = 11,       /* a single-CTA tensor-core Gram with fewer tiles than SMs (few
                                     variables, many samples) is split over sample ranges, each
                                     part's exact int32 counts in its own workspace slice, summed by
                                     the MI (or counts) kernel: 0 = automatic (default), 1 = never,
                                     2 = whenever there are samples enough                        */
+    GBMI_OPT_FP4 = 12            /* 1: the tensor-core paths (single calls, cross, host buffers,
+                                    out-of-core, CSR densified, batches and servers created while
+                                    it is set; not mi_all_pairs_noalloc or GBMI_OPT_DIRECT)
+                                    pack X as FP4 (E2M1 0 / 1, two samples per byte) and run the
+                                    block-scaled FP4 MMA (tcgen05 kind::mxf4, every scale factor
+                                    1.0; tiles at most 240 wide): the same exact counts from half
+                                    the operand bytes, about 1.7x the FP8 Gram's rate; 0: FP8
+                                    operands (default 1)                                          */
 } gbmi_option;
 
 /* ---------------------------------------------------------------- core calls */
@@ -212,7 +221,7 @@ gbmi_status gbmi_counts_all_pairs_csr(const int64_t* row_ptr, const int32_t* col
 /* ------------------------------------------------------ counts and pieces */
 
 /* Co-occurrence counts N11 = X^T X (G11 of Sec. 2 step 2) as int32, n x n,
- * both triangles written.  path = GBMI_PATH_PLAIN (tensor cores, FP8 operands,
+ * both triangles written.  path = GBMI_PATH_PLAIN (tensor cores, FP4 or FP8 operands,
  * FP32 accumulation in exact chunks) or GBMI_PATH_POPCOUNT (bit-packed AND +
  * popcount).  Both must agree bit for bit. */
 gbmi_status gbmi_counts_all_pairs(const uint8_t* X, int64_t m, int64_t n, int32_t* n11, int path);

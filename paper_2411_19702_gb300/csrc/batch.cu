@@ -2,7 +2,8 @@
 // pipeline captured in a CUDA graph (see gbmi_batch_* in gbmi.h).
 //
 // Plan layout in one workspace:
-//   P      every job's K-block-major FP8 operand(s), one after another, so one
+//   P      every job's K-block-major operand(s), FP4 (the default) or FP8 as
+//          GBMI_OPT_FP4 was when the plan was made, one after another, so one
 //          set of TMA descriptors reaches all of them;
 //   v      every operand's column counts, one after another;
 //   vars   the per-variable epilogue terms, same indexing as v;
@@ -31,7 +32,8 @@ struct gbmi_batch {
     std::vector<int> pack_of_x, pack_of_y;   // pack-job index of each job's X and Y
     int64_t total_rows = 0, total_vars = 0, total_ctas = 0;
     int64_t num_tiles = 0;
-    int64_t pair_tiles = 0;   // tiles [0, pair_tiles) run on CTA pairs (256 x 256)
+    int64_t pair_tiles = 0;   // tiles [0, pair_tiles) run on CTA pairs (256 x 256 or 240)
+    bool fp4 = false;         // operands in the FP4 form
     int grid = 0, pair_grid = 0;
     gbmi::OperandMaps maps;
     cudaStream_t cap = nullptr;
@@ -98,6 +100,7 @@ gbmi_status enqueue(gbmi_batch* b, cudaStream_t s, unsigned int* err) {
     L.jobs = static_cast<const GramJob*>(b->gramjobs.p);
     L.mode = kTcModeMI;
     L.fixup = b->hgram.empty() ? 0 : b->hgram[0].mp.fixup;   // one setting for every job
+    L.fp4 = b->fp4 ? 1 : 0;
     L.err = err;
     L.timeout_ns = rt::g_opt.timeout_ns;
     L.debug_flags = rt::g_opt.debug_flags;
@@ -142,6 +145,9 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
     }
 
     // ---- layout
+    const bool fp4 = rt::g_opt.fp4 != 0;
+    const int bn_max = fp4 ? kTcBNFp4 : kTcBNMax;
+    b->fp4 = fp4;
     int64_t rows = 0, vars = 0;
     auto add_operand = [&](const uint8_t* X, int64_t m, int64_t n, const MiParams& mp) {
         PackJob pj;
@@ -150,7 +156,8 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
         pj.n = n;
         pj.ldx = n;
         pj.rows_p = pack_rows(n);
-        pj.ldp = pack_ld(m);
+        pj.ldp = pack_ld_of(m, fp4);
+        pj.fp4 = fp4 ? 1 : 0;
         set_pack_pointers(pj, X);
         pj.P = reinterpret_cast<uint8_t*>(rows * kTcBK);        // offset; rebased below
         pj.v = reinterpret_cast<int32_t*>(vars * 4);            // offset; rebased below
@@ -158,7 +165,7 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
         b->hvarbegin.push_back(vars);
         b->hparams.push_back(mp);
         const int64_t row0 = rows, var0 = vars;
-        rows += (pj.ldp / kTcBK) * pj.rows_p;
+        rows += (pj.ldp / kb_samples(fp4)) * pj.rows_p;
         vars += n;
         return std::make_pair(row0, var0);
     };
@@ -183,11 +190,11 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
         g.strideA = pack_rows(j.n);
         g.strideB = pack_rows(nb);
         g.k_begin = 0;
-        g.k_blocks = static_cast<int32_t>(pack_ld(j.m) / kTcBK);
+        g.k_blocks = static_cast<int32_t>(pack_ld_of(j.m, fp4) / kb_samples(fp4));
         g.n_a = static_cast<int32_t>(j.n);
         g.n_b = static_cast<int32_t>(nb);
         g.symmetric = sym ? 1 : 0;
-        g.bn = rt::choose_bn(j.m, j.n, nb, sym);
+        g.bn = std::min(rt::choose_bn(j.m, j.n, nb, sym), bn_max);
         g.va = reinterpret_cast<const MiVar*>(xa.second * sizeof(MiVar));   // rebased below
         g.vb = reinterpret_cast<const MiVar*>(yb.second * sizeof(MiVar));
         g.ld_out = nb;
@@ -200,11 +207,11 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
     b->hvarbegin.push_back(vars);
     if (rows >= (int64_t{1} << 31)) {
         delete b;
-        return fail(GBMI_ERR_ARG, "batch operands exceed 2^31 rows of 128 samples");
+        return fail(GBMI_ERR_ARG, "batch operands exceed 2^31 rows of 128 bytes");
     }
 
     // ---- device buffers, with the offsets above turned into pointers
-    st = ensure(b->P, static_cast<size_t>(rows) * kTcBK, "batch FP8 operands");
+    st = ensure(b->P, static_cast<size_t>(rows) * kTcBK, "batch operands");
     if (st == GBMI_OK) st = ensure(b->v, static_cast<size_t>(vars) * 4, "batch column counts");
     if (st == GBMI_OK) st = ensure(b->vars, static_cast<size_t>(vars) * sizeof(MiVar), "batch terms");
     if (st == GBMI_OK) st = ensure(b->sched, 256, "batch tile counter");
@@ -237,7 +244,8 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
     }
 
     // ---- tiles.  Jobs whose both sides span at least kPairMinN variables run
-    // on CTA pairs (256 x 256 tiles, half the operand bytes per SM per MMA) in
+    // on CTA pairs (256 x 256 tiles, 256 x 240 for FP4; half the operand bytes
+    // per SM per MMA) in
     // a first launch; the rest on single-CTA tiles of their own width in a
     // second.  Within each launch, jobs by descending per-tile cost, each job
     // in its own order.
@@ -248,7 +256,7 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
         GramJob& g = b->hgram[i];
         if (pairs_ok && (rt::g_opt.pair == 2 || (g.n_a >= kPairMinN && g.n_b >= kPairMinN))) {
             pair_job[i] = 1;
-            g.bn = kTcBNMax;
+            g.bn = bn_max;
         }
     }
     auto tile_m = [&](int i) { return pair_job[i] ? 2 * kTcBM : kTcBM; };

@@ -53,9 +53,11 @@ gbmi_status check_sizes(int64_t m, int64_t n1, int64_t n2) {
     return GBMI_OK;
 }
 
-// Pack one operand: the FP8 operand into P (at row p_row of the K-block-major
-// buffer) and/or the bit-packed operand into B, and the column counts into v.
-gbmi_status pack(const uint8_t* X, int64_t m, int64_t n, uint8_t* P, uint32_t* B, int32_t* v) {
+// Pack one operand: the FP8 (fp4: FP4) operand into P (at row p_row of the
+// K-block-major buffer) and/or the bit-packed operand into B, and the column
+// counts into v.
+gbmi_status pack(const uint8_t* X, int64_t m, int64_t n, uint8_t* P, uint32_t* B, int32_t* v,
+                 bool fp4 = false) {
     GBMI_LAUNCH(launch_zero_u32(v, n, g_stream), "zero");
     PackJob j;
     std::memset(&j, 0, sizeof(j));
@@ -67,7 +69,8 @@ gbmi_status pack(const uint8_t* X, int64_t m, int64_t n, uint8_t* P, uint32_t* B
     j.Bp = B;
     j.v = v;
     j.rows_p = pack_rows(n);
-    j.ldp = pack_ld(m);
+    j.ldp = pack_ld_of(m, fp4);
+    j.fp4 = fp4 ? 1 : 0;
     GBMI_LAUNCH(launch_pack(j, g_stream), "pack");
     return GBMI_OK;
 }
@@ -110,11 +113,13 @@ gbmi_status tile_list(DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn, 
 // The CTA-pair kernel streams half the operand bytes per SM per MMA, so it is
 // taken whenever its launch keeps at least as many SMs busy as the single-CTA
 // launch of the same problem would (small problems keep the finer tiles).
-bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn) {
+// bn_max: the pair's tile width (256; 240 for FP4 operands).
+bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn,
+              int bn_max = kTcBNMax) {
     if (g_opt.pair == 0 || c.pair_clusters <= 0) return false;
     if (g_opt.pair == 2) return true;   // forced (tests)
     if (g_opt.tile_n != 0) return false;   // a forced tile width names a single-CTA tile
-    const int64_t pair_tiles = gram_tile_count(n_a, n_b, kTcBNMax, sym, 2 * kTcBM);
+    const int64_t pair_tiles = gram_tile_count(n_a, n_b, bn_max, sym, 2 * kTcBM);
     const int64_t single_tiles = gram_tile_count(n_a, n_b, bn, sym, kTcBM);
     const int64_t pair_sms = 2 * std::min<int64_t>(pair_tiles, c.pair_clusters);
     return pair_sms >= std::min<int64_t>(single_tiles, c.sm_count);
@@ -139,14 +144,18 @@ bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn) {
 // by a model: the makespan of ceil(S * tiles / units) waves of units 1/S as
 // long, plus the slices' traffic (written by the Gram, read by the final
 // kernel: about 3 x S x n_a x n_b x 4 bytes at HBM rate); a split is taken
-// only when the model gains at least 10% over one part.
-int split_parts(int units, int tiles, int64_t kb_total, int64_t n_a, int64_t n_b) {
-    constexpr int64_t kMinPartKb = 16;     // 2048 samples per part at least
+// only when the model gains at least 10% over one part.  spk: samples per K
+// block (128 FP8, 256 FP4).
+int split_parts(int units, int tiles, int64_t kb_total, int64_t n_a, int64_t n_b,
+                int64_t spk = kKbSamplesFp8) {
+    const int64_t kMinPartKb = std::max<int64_t>(1, 2048 / spk);   // 2048 samples per part
     constexpr int64_t kMaxParts = 128;
     constexpr int64_t kMaxSliceBytes = int64_t{2} << 30;
-    constexpr double kBlockSeconds = 0.29e-6;   // one 128-sample K block of one tile unit
+    // one K block of one tile unit (FP8: 128 samples; FP4: 256 samples at
+    // about twice the rate)
+    constexpr double kBlockSeconds = 0.29e-6;
     constexpr double kHbmBytesPerSecond = 6.0e12;
-    const int64_t kb_chunk = kExactChunk / kTcBK;
+    const int64_t kb_chunk = kExactChunk / spk;
     if (g_opt.split_k == 1 || tiles <= 0 || units <= 0) return 1;
     if (g_opt.split_k != 2 && tiles >= units) return 1;
     const int64_t exact = (kb_total + kb_chunk - 1) / kb_chunk;   // parts of at most 2^24
@@ -176,13 +185,13 @@ int split_parts(int units, int tiles, int64_t kb_total, int64_t n_a, int64_t n_b
 }
 
 gbmi_status run_gram_split(DeviceCtx& c, const OperandMaps& maps, const GramJob& proto, int bn,
-                           bool pair, int tiles, int64_t kb_total, int S, int mode) {
+                           bool pair, int tiles, int64_t kb_total, int S, int mode, bool fp4) {
     const int64_t slice = static_cast<int64_t>(proto.n_a) * proto.n_b;
     // its own buffer: the caller's counts may live in the workspace's count matrix
     GBMI_TRY(ensure(c.split_part, static_cast<size_t>(S) * slice * 4, "split partial counts"));
     int32_t* part = static_cast<int32_t*>(c.split_part.p);
     const int64_t kb_s = (kb_total + S - 1) / S;   // every part non-empty (split_parts)
-    if ((S - 1) * kb_s >= kb_total || kb_s > kExactChunk / kTcBK)
+    if ((S - 1) * kb_s >= kb_total || kb_s > kExactChunk / kb_samples(fp4))
         return fail(GBMI_ERR_ARG, "internal: bad sample split");
     c.split_jobs_host.assign(static_cast<size_t>(S), proto);
     for (int s = 0; s < S; ++s) {
@@ -220,6 +229,7 @@ gbmi_status run_gram_split(DeviceCtx& c, const OperandMaps& maps, const GramJob&
     L.tiles = static_cast<const GramTile*>(c.split_tiles.p);
     L.num_tiles = S * tiles;
     L.pair = pair ? 1 : 0;
+    L.fp4 = fp4 ? 1 : 0;
     L.mode = kTcModeCounts;
     L.err = static_cast<unsigned int*>(c.err.p);
     L.timeout_ns = g_opt.timeout_ns;
@@ -250,25 +260,29 @@ gbmi_status run_gram_split(DeviceCtx& c, const OperandMaps& maps, const GramJob&
 
 gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int64_t m,
                      int mode, const OperandMaps* dmaps = nullptr, int shard = 0,
-                     int num_shards = 1) {
+                     int num_shards = 1, bool fp4 = false) {
     OperandMaps maps;
     if (dmaps != nullptr)
         maps = *dmaps;
     else if (!make_operand_maps(&maps, static_cast<const uint8_t*>(c.P.p), total_rows))
         return fail(GBMI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    // CTA pairs: 256 x 256 tiles on clusters of two SMs (packed operands only)
+    // CTA pairs: 256 x 256 tiles (256 x 240 for FP4 operands) on clusters of
+    // two SMs (packed operands only)
+    const int bn_max = fp4 ? kTcBNFp4 : kTcBNMax;
     const bool pair = dmaps == nullptr &&
-                      use_pair(c, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn);
-    const int64_t kb_all = pack_ld(m) / kTcBK;
-    const int bn = pair ? kTcBNMax : proto.bn;
+                      use_pair(c, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn, bn_max);
+    const int64_t spk = kb_samples(fp4);
+    const int64_t kb_all = pack_ld_of(m, fp4) / spk;
+    const int bn = pair ? bn_max : std::min(proto.bn, bn_max);
     const int bm = pair ? 2 * kTcBM : kTcBM;
     int tiles = 0;
     GBMI_TRY(tile_list(c, proto.n_a, proto.n_b, proto.symmetric != 0, bn, &tiles, bm));
     if (dmaps == nullptr && num_shards == 1 && proto.out_t == nullptr &&
         (mode == kTcModeMI || mode == kTcModeCounts)) {
         const int S = split_parts(pair ? c.pair_clusters : c.sm_count, tiles, kb_all,
-                                  proto.n_a, proto.n_b);
-        if (S > 1) return run_gram_split(c, maps, proto, bn, pair, tiles, kb_all, S, mode);
+                                  proto.n_a, proto.n_b, spk);
+        if (S > 1)
+            return run_gram_split(c, maps, proto, bn, pair, tiles, kb_all, S, mode, fp4);
     }
     GramLaunch L;
     std::memset(&L, 0, sizeof(L));
@@ -276,6 +290,7 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     L.job0 = proto;
     L.job0.bn = bn;
     L.pair = pair ? 1 : 0;
+    L.fp4 = fp4 ? 1 : 0;
     L.fixup = proto.mp.fixup;
     const int64_t t0 = static_cast<int64_t>(tiles) * shard / num_shards;
     const int64_t t1 = static_cast<int64_t>(tiles) * (shard + 1) / num_shards;
@@ -288,8 +303,8 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     L.direct = dmaps != nullptr ? 1 : 0;
     GBMI_TRY(ensure(c.sched, 256, "tile counter"));
     L.counter = static_cast<unsigned int*>(c.sched.p);
-    const int64_t kb_total = pack_ld(m) / kTcBK;
-    const int64_t kb_chunk = kExactChunk / kTcBK;
+    const int64_t kb_total = kb_all;
+    const int64_t kb_chunk = kExactChunk / spk;
     int32_t* prefix = nullptr;   // MI over several chunks: counts of the earlier ones
     if (mode == kTcModeMI && kb_total > kb_chunk) {
         GBMI_TRY(ensure(c.counts, static_cast<size_t>(proto.n_a) * proto.n_b * 4,
@@ -324,9 +339,11 @@ int choose_path(int path, int64_t m, int64_t n1, int64_t n2) {
 
 // Workspace layout of the tensor-core path: X's operand rows, then Y's; or,
 // for the direct path, the tensor maps over X and Y themselves.
+// fp4: the packed operands are the FP4 form (kb counts 256-sample blocks).
 struct TcLayout {
-    int64_t kb, rows_a, rows_b, total_rows;
-    bool direct;
+    int64_t kb = 0, rows_a = 0, rows_b = 0, total_rows = 0;
+    bool direct = false;
+    bool fp4 = false;
     OperandMaps maps;
 };
 
@@ -362,20 +379,21 @@ gbmi_status tc_prepare(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int64_t
         }
         return GBMI_OK;
     }
-    L->kb = pack_ld(m) / kTcBK;
+    L->fp4 = g_opt.fp4 != 0;
+    L->kb = pack_ld_of(m, L->fp4) / kb_samples(L->fp4);
     L->rows_a = pack_rows(n1);
     L->rows_b = sym ? 0 : pack_rows(n2);
     L->total_rows = L->kb * (L->rows_a + L->rows_b);
     if (L->total_rows >= (int64_t{1} << 31))
-        return fail(GBMI_ERR_ARG, "packed operands exceed 2^31 rows of 128 samples");
-    GBMI_TRY(ensure(c.P, static_cast<size_t>(L->total_rows) * kTcBK, "FP8 operand"));
+        return fail(GBMI_ERR_ARG, "packed operands exceed 2^31 rows of 128 bytes");
+    GBMI_TRY(ensure(c.P, static_cast<size_t>(L->total_rows) * kTcBK, "packed operand"));
     GBMI_TRY(ensure(c.va, static_cast<size_t>(n1) * 4, "column counts"));
     uint8_t* P = static_cast<uint8_t*>(c.P.p);
-    GBMI_TRY(pack(X, m, n1, P, nullptr, static_cast<int32_t*>(c.va.p)));
+    GBMI_TRY(pack(X, m, n1, P, nullptr, static_cast<int32_t*>(c.va.p), L->fp4));
     if (!sym) {
         GBMI_TRY(ensure(c.vb, static_cast<size_t>(n2) * 4, "column counts"));
         GBMI_TRY(pack(Y, m, n2, P + L->kb * L->rows_a * kTcBK, nullptr,
-                      static_cast<int32_t*>(c.vb.p)));
+                      static_cast<int32_t*>(c.vb.p), L->fp4));
     }
     return GBMI_OK;
 }
@@ -456,13 +474,14 @@ gbmi_status mi_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n1, i
         const int bn = rt::choose_bn(m, n1, n2, sym);
         if (path == GBMI_PATH_FUSED)
             return run_gram(c, L.total_rows, tc_job(L, m, n1, n2, sym, bn, va, vb, mp, out, nullptr),
-                            m, kTcModeMI, L.direct ? &L.maps : nullptr, shard, num_shards);
+                            m, kTcModeMI, L.direct ? &L.maps : nullptr, shard, num_shards,
+                            L.fp4);
         // plain: exact counts to HBM, then the elementwise MI kernel
         GBMI_TRY(ensure(c.counts, static_cast<size_t>(n1) * n2 * 4, "count matrix"));
         int32_t* N11 = static_cast<int32_t*>(c.counts.p);
         GBMI_TRY(run_gram(c, L.total_rows,
                           tc_job(L, m, n1, n2, sym, bn, va, vb, mp, nullptr, N11), m,
-                          kTcModeCounts, L.direct ? &L.maps : nullptr));
+                          kTcModeCounts, L.direct ? &L.maps : nullptr, 0, 1, L.fp4));
         if (sym)
             GBMI_LAUNCH(launch_mi_from_counts_sym(N11, n2, va, n1, mp, out, n2, g_stream),
                         "mi_from_counts");
@@ -544,7 +563,7 @@ gbmi_status counts_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t n
     const MiParams mp = rt::mi_params_plain(m, 0, nullptr);
     const int bn = rt::choose_bn(m, n1, n2, sym);
     return run_gram(c, L.total_rows, tc_job(L, m, n1, n2, sym, bn, nullptr, nullptr, mp, nullptr, n11),
-                    m, kTcModeCounts, L.direct ? &L.maps : nullptr);
+                    m, kTcModeCounts, L.direct ? &L.maps : nullptr, 0, 1, L.fp4);
 }
 
 // Resources of the host-buffer pipeline (created once per device context).
@@ -591,14 +610,16 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
                            int64_t n1, int64_t n2, float* out, bool sym) {
     TcLayout L;
     L.direct = false;
-    L.kb = pack_ld(m) / kTcBK;
+    L.fp4 = g_opt.fp4 != 0;
+    const int64_t spk = kb_samples(L.fp4);
+    L.kb = pack_ld_of(m, L.fp4) / spk;
     L.rows_a = pack_rows(n1);
     L.rows_b = sym ? 0 : pack_rows(n2);
     L.total_rows = L.kb * (L.rows_a + L.rows_b);
     if (L.total_rows >= (int64_t{1} << 31))
-        return fail(GBMI_ERR_ARG, "packed operands exceed 2^31 rows of 128 samples");
+        return fail(GBMI_ERR_ARG, "packed operands exceed 2^31 rows of 128 bytes");
     const size_t ob = static_cast<size_t>(n1) * n2 * 4;
-    GBMI_TRY(ensure(c.P, static_cast<size_t>(L.total_rows) * kTcBK, "FP8 operand"));
+    GBMI_TRY(ensure(c.P, static_cast<size_t>(L.total_rows) * kTcBK, "packed operand"));
     GBMI_TRY(ensure(c.Xs, static_cast<size_t>(m) * n1, "input staging"));
     GBMI_TRY(ensure(c.va, static_cast<size_t>(n1) * 4, "column counts"));
     if (!sym) {
@@ -609,19 +630,20 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
     MiParams mp;
     GBMI_TRY(rt::mi_params(c, m, &mp));
 
-    // upload chunks (rows, multiples of 128) and Gram chunks (groups of them)
-    const int64_t R = std::max<int64_t>(kTcBK * 64, round_up((m + kUploadChunks - 1) / kUploadChunks,
-                                                              kTcBK));
+    // upload chunks (rows, whole K blocks) and Gram chunks (groups of them)
+    const int64_t R = std::max<int64_t>(spk * 64, round_up((m + kUploadChunks - 1) / kUploadChunks,
+                                                            spk));
     const int uchunks = static_cast<int>((m + R - 1) / R);
     // the FP64-combine kernel variant has no prefix input: one Gram launch then
     const int gchunks = mp.fixup ? 1 : std::min(kGramChunks, uchunks);
     if (gchunks > 1) GBMI_TRY(ensure(c.counts, ob, "count matrix"));
 
     // tiles in panel-major order
-    const int bn_single = rt::choose_bn(m, n1, n2, sym);
-    const bool pair = use_pair(c, n1, n2, sym, bn_single);
+    const int bn_max = L.fp4 ? kTcBNFp4 : kTcBNMax;
+    const int bn_single = std::min(rt::choose_bn(m, n1, n2, sym), bn_max);
+    const bool pair = use_pair(c, n1, n2, sym, bn_single, bn_max);
     const int bm = pair ? 2 * kTcBM : kTcBM;
-    const int bn = pair ? kTcBNMax : bn_single;
+    const int bn = pair ? bn_max : bn_single;
     const int64_t TI = (n1 + bm - 1) / bm, TJ = (n2 + bn - 1) / bn;
     const int64_t pblocks = std::max<int64_t>(1, (TI + 7) / 8);   // about eight panels
     const int64_t panels = (TI + pblocks - 1) / pblocks;
@@ -675,10 +697,11 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
         j.m = rows;
         j.n = n;
         j.ldx = n;
-        j.P = Pop + (r0 / kTcBK) * rows_p * kTcBK;
+        j.P = Pop + (r0 / spk) * rows_p * kTcBK;
         j.v = v;
         j.rows_p = rows_p;
-        j.ldp = pack_ld(rows);
+        j.ldp = pack_ld_of(rows, L.fp4);
+        j.fp4 = L.fp4 ? 1 : 0;
         GBMI_LAUNCH(launch_pack(j, g_stream), "pack");
         return GBMI_OK;
     };
@@ -699,6 +722,7 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
     G.timeout_ns = g_opt.timeout_ns;
     G.debug_flags = g_opt.debug_flags;
     G.pair = pair ? 1 : 0;
+    G.fp4 = L.fp4 ? 1 : 0;
     G.fixup = mp.fixup;
     G.counter = static_cast<unsigned int*>(c.sched.p);
     const int grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, G.num_tiles))
@@ -714,8 +738,8 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
                                      P + L.kb * L.rows_a * kTcBK, L.rows_b,
                                      static_cast<int32_t*>(c.vb.p)));
         }
-        const int64_t kb0 = (u0 * R) / kTcBK;
-        const int64_t kb1 = g + 1 < gchunks ? (u1 * R) / kTcBK : L.kb;
+        const int64_t kb0 = (u0 * R) / spk;
+        const int64_t kb1 = g + 1 < gchunks ? (u1 * R) / spk : L.kb;
         G.job0.k_begin = static_cast<int32_t>(kb0);
         G.job0.k_blocks = static_cast<int32_t>(kb1 - kb0);
         if (g + 1 < gchunks) {   // counts of this sample chunk, kept in HBM
@@ -882,10 +906,11 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
         g.n_a = static_cast<int32_t>(rows);
         g.n_b = static_cast<int32_t>(w);
         g.symmetric = 0;
-        g.bn = rt::choose_bn(m, rows, w, false);
+        const int bn_max = L.fp4 ? kTcBNFp4 : kTcBNMax;
+        g.bn = std::min(rt::choose_bn(m, rows, w, false), bn_max);
         if (L.direct && g.bn < kTcBM) g.bn = kTcBM;
-        if (!L.direct && use_pair(c, rows, w, false, g.bn)) {
-            g.bn = kTcBNMax;
+        if (!L.direct && use_pair(c, rows, w, false, g.bn, bn_max)) {
+            g.bn = bn_max;
             pair_panel[static_cast<size_t>(p)] = 1;
         }
         g.va = va + i0;
@@ -958,6 +983,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
             G.timeout_ns = g_opt.timeout_ns;
             G.debug_flags = g_opt.debug_flags;
             G.direct = L.direct ? 1 : 0;
+            G.fp4 = L.fp4 ? 1 : 0;
             G.pair = pair_panel[p];
             G.fixup = mp.fixup;
             G.counter = static_cast<unsigned int*>(c.sched.p);
@@ -1242,6 +1268,9 @@ gbmi_status gbmi_set_option(int option, int64_t value) {
         case GBMI_OPT_SPLIT_K:
             if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "split mode must be 0, 1 or 2");
             g_opt.split_k = static_cast<int>(value);
+            return GBMI_OK;
+        case GBMI_OPT_FP4:
+            g_opt.fp4 = value != 0 ? 1 : 0;
             return GBMI_OK;
         case GBMI_OPT_CSR_PATH:
             if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "CSR path must be 0, 1 or 2");

@@ -4,16 +4,19 @@
 // Sec. 3.1, with everything after it done per tile while it is on chip).
 //
 // Operands: K-block-major packed matrices (for each block of 128 samples, one
-// 128-byte row per variable, FP8 E4M3 0x00/0x38), or, on the direct path, the
-// caller's row-major uint8 0/1 matrix itself read as MN-major E4M3 (a byte 1
-// is the subnormal 2^-9; counts come out scaled by 2^-18, still exact; the
-// epilogue scales them back).  0 and 1 are exact in
-// E4M3, every product is 0 or 1 and the FP32 accumulator holds integers
-// exactly below 2^24, so a tile's counts are exact as long as one launch
-// accumulates at most 2^24 samples (k_blocks * 128).  One launch can serve
-// many datasets: every tile names its job (dataset), whose descriptor gives
-// the operands' first rows in the shared buffer, its sample range, its tile
-// width bn (64, 128 or 256), its epilogue terms and its output.
+// 128-byte row per variable, FP8 E4M3 0x00/0x38), or their FP4 form (for each
+// block of 256 samples, one 128-byte row of E2M1 nibbles 0x0/0x2, multiplied
+// by the block-scaled MMA kind::mxf4 with every scale factor 1.0), or, on the
+// direct path, the caller's row-major uint8 0/1 matrix itself read as MN-major
+// E4M3 (a byte 1 is the subnormal 2^-9; counts come out scaled by 2^-18, still
+// exact; the epilogue scales them back).  0 and 1 are exact in E4M3 and E2M1,
+// every product is 0 or 1 and the FP32 accumulator holds integers exactly
+// below 2^24, so a tile's counts are exact as long as one launch accumulates
+// at most 2^24 samples (k_blocks x 128 or 256).  One launch can serve many
+// datasets: every tile names its job (dataset), whose descriptor gives the
+// operands' first rows in the shared buffer, its sample range, its tile width
+// bn (64, 128 or 256; at most 240 in an FP4 launch), its epilogue terms and its
+// output.
 //
 // Persistent, warp-specialised CTA, one per SM (576 threads; 320 for the
 // variant with the FP64 combine), or CTA pairs (clusters of 2, kPair):
@@ -28,7 +31,10 @@
 //               pair, CTA 0 issues cta_group::2 M=256 N=256) into one of two
 //               256-column FP32 accumulators, commits each stage back to the
 //               ring and each finished tile to the epilogue.  The ragged last
-//               column block runs at its valid width rounded up to 32.
+//               column block runs at its valid width rounded up to 32.  FP4
+//               launches issue kind::mxf4.block_scale K=64 instead (N <= 240;
+//               the scale factors, all 1.0, sit in columns 240-255 and 496-511,
+//               filled by the epilogue warps before the first MMA).
 //   warps 2-17  epilogue (warps 2-9 for the FP64-combine variant), four (two)
 //               warps per TMEM lane quadrant (tcgen05.ld only reaches lanes
 //               32*(warp%4)..+31), each taking a quarter (half) of the tile's
@@ -75,10 +81,15 @@ __host__ __device__ constexpr bool is_mi() { return kMode == kTcModeMI || kMode 
 // 576 threads and keeps 8.
 __host__ __device__ constexpr int epi_warps(int mode) { return mode == kTcModeMI ? 8 : 16; }
 __host__ __device__ constexpr int threads_of(int mode) { return 64 + 32 * epi_warps(mode); }
-constexpr int kUmmaK = 32;                       // K per MMA for 8-bit inputs
+constexpr int kUmmaK = 32;                       // bytes of K per MMA (32 FP8 or 64 FP4 samples)
 constexpr int kABytes = kTcBM * kTcBK;           // 16 KB: 128 rows of A
 constexpr int kAccCols = kTcBNMax;               // TMEM columns per accumulator buffer
 constexpr int kTmemCols = 2 * kAccCols;          // 512: the whole tensor memory
+// FP4 launches: scale factors (all 1.0, UE8M0 0x7F) in the 16 columns after
+// each accumulator's first 240; A's in buffer 0's, B's in buffer 1's
+constexpr int kSfaCol = kTcBNFp4;
+constexpr int kSfbCol = kAccCols + kTcBNFp4;
+constexpr uint32_t kScaleOnes = 0x7F7F7F7Fu;
 constexpr size_t kColVarTotal = 32768;           // staged column terms of all epilogue warps
 constexpr int kGroup = 16;                       // accumulator columns per tcgen05.ld
 constexpr int kQ = 8;                            // tile-id queue between the roles
@@ -155,12 +166,13 @@ __device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
 
 // MMA width of a tile: the job's tile width, or, for the ragged last column
 // block, its valid columns rounded up to 32 (a valid N for M = 128 on one CTA
-// and M = 256 on a pair); the columns beyond are masked by every epilogue.
+// and M = 256 on a pair), at most the tile width (240 = 15 x 16 is valid for
+// both); the columns beyond are masked by every epilogue.
 __device__ __forceinline__ int tile_n(const GramJob& job, const GramTile& tile) {
     const int64_t w = static_cast<int64_t>(job.n_b) - static_cast<int64_t>(tile.J) * job.bn;
     if (w >= job.bn) return job.bn;
     const int n = static_cast<int>((w + 31) / 32 * 32);
-    return n < 32 ? 32 : n;
+    return n < 32 ? 32 : (n > job.bn ? job.bn : n);
 }
 
 // ------------------------------------------------------------------ producer
@@ -218,9 +230,13 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         const GramTile tile = L.tiles[tid];
         const GramJob& job = job_of(L, tile.job);
         const int bn = job.bn;
-        const CUtensorMap* mapB = bn == 256 ? &maps.box256 : (bn == 128 ? &maps.box128
-                                                                         : &maps.box64);
-        const uint32_t bytes = static_cast<uint32_t>((Plan<kPair>::tile_m + bn) * kTcBK);
+        // rows of B per stage: the tile width, 256 for a 240-wide FP4 tile (its
+        // MMAs read the first 240); a pair loads four 128-row boxes
+        const int brows = bn > kTcBM ? kTcBNMax : bn;
+        const CUtensorMap* mapB = brows == 256 ? &maps.box256 : (brows == 128 ? &maps.box128
+                                                                               : &maps.box64);
+        const uint32_t bytes = static_cast<uint32_t>(
+            (Plan<kPair>::tile_m + (kPair ? 2 * kTcBM : brows)) * kTcBK);
         const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m;
         const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn;
         // pair: the partner CTA holds B rows [N/2, N) of the tile's MMA width N
@@ -292,7 +308,9 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
 }
 
 // ------------------------------------------------------------------ MMA issuer
-template <bool kPair>
+// kFp4: the launch's operands are the FP4 form (block-scaled MMA); one copy of
+// the issue loop per form, so the per-K-block loop carries no branch on it.
+template <bool kPair, bool kFp4>
 __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tmem_base) {
     constexpr int kStages = Plan<kPair>::stages;
     int stage = 0;
@@ -316,10 +334,13 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
         if (t < 0) break;
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
+        const uint32_t mma_n = static_cast<uint32_t>(tile_n(job, tile));
         const uint32_t idesc =
-            kPair ? ptx::idesc_e4m3_f32(2 * kTcBM, static_cast<uint32_t>(tile_n(job, tile)))
+            kFp4 ? ptx::idesc_mxf4_f32(kPair ? 2 * kTcBM : kTcBM, mma_n)
+            : kPair ? ptx::idesc_e4m3_f32(2 * kTcBM, mma_n)
             : L.direct ? ptx::idesc_e4m3_f32_mnmajor(kTcBM, static_cast<uint32_t>(job.bn))
-                       : ptx::idesc_e4m3_f32(kTcBM, static_cast<uint32_t>(tile_n(job, tile)));
+                       : ptx::idesc_e4m3_f32(kTcBM, mma_n);
+        const uint32_t sfa = tmem_base + kSfaCol, sfb = tmem_base + kSfbCol;
         const int k_blocks = job.k_blocks;
         if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, L.timeout_ns,
                                     sm.abort_flag())) {
@@ -338,13 +359,22 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
             if constexpr (kPair) {
                 const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
                 const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
+                if constexpr (kFp4) {
 #pragma unroll
-                for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
-                    const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
-                    ptx::mma_f8f6f4_pair(d_tmem, adesc + off, bdesc + off, idesc,
-                                         (kb | kk) != 0 ? 1u : 0u);
+                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+                        ptx::mma_mxf4_pair(d_tmem, adesc + off, bdesc + off, idesc, sfa, sfb,
+                                           (kb | kk) != 0 ? 1u : 0u);
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+                        ptx::mma_f8f6f4_pair(d_tmem, adesc + off, bdesc + off, idesc,
+                                             (kb | kk) != 0 ? 1u : 0u);
+                    }
                 }
-            } else if (L.direct) {
+            } else if (!kFp4 && L.direct) {
                 // MN-major: 128-sample K-rows of 128 bytes, 128-variable atoms of
                 // B 16 KB apart; K step kk starts kk * 32 rows (4 atoms) further
                 const uint64_t adesc =
@@ -360,12 +390,21 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
             } else {
                 const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
                 const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
+                if constexpr (kFp4) {
 #pragma unroll
-                for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
-                    // advance the start address by kk * 32 bytes inside the swizzle row
-                    const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
-                    ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
-                                    (kb | kk) != 0 ? 1u : 0u);
+                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+                        ptx::mma_mxf4(d_tmem, adesc + off, bdesc + off, idesc, sfa, sfb,
+                                      (kb | kk) != 0 ? 1u : 0u);
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+                        // advance the start address by kk * 32 bytes inside the swizzle row
+                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+                        ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
+                                        (kb | kk) != 0 ? 1u : 0u);
+                    }
                 }
             }
             if constexpr (kPair)
@@ -454,8 +493,10 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
         // copies in registers: the epilogue's stores could otherwise alias the
         // job table and force these fields to be reloaded after every store
         const MiParams P = job.mp;
-        const int cols = job.bn / kParts;              // columns of this warp
-        const int col_base = part * cols;
+        // columns of this warp: a multiple of 16 (240-wide tiles: 64, 64, 64, 48)
+        const int per = ((job.bn / kParts) + 15) & ~15;
+        const int col_base = part * per;
+        const int cols = max(0, min(per, job.bn - col_base));
         const int64_t n_a = job.n_a, n_b = job.n_b;
         const bool sym = job.symmetric != 0;
         const int64_t ibase = static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m +
@@ -780,12 +821,31 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
     if constexpr (kPair) ptx::cluster_sync();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *sm.tmem_holder();
+    if (L.fp4) {
+        // every scale factor of the block-scaled MMA is 1.0: four epilogue warps
+        // (one per TMEM lane quadrant) fill the two 16-column scale regions
+        if (warp >= 2 && warp < 6) {
+            const uint32_t lanes = static_cast<uint32_t>((warp & 3) * 32) << 16;
+            ptx::tmem_st_32x32b_x16_fill(tmem_base + lanes + kSfaCol, kScaleOnes);
+            ptx::tmem_st_32x32b_x16_fill(tmem_base + lanes + kSfbCol, kScaleOnes);
+            ptx::tmem_wait_st();
+        }
+        ptx::tc_fence_before();
+        __syncthreads();
+        if constexpr (kPair) ptx::cluster_sync();
+        ptx::tc_fence_after();
+    }
 
     if (warp == 0) {
         if (lane == 0 && lead) run_producer<kPair>(sm, maps, L);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0 && lead) run_mma<kPair>(sm, L, tmem_base);
+        if (lane == 0 && lead) {
+            if (L.fp4)
+                run_mma<kPair, true>(sm, L, tmem_base);
+            else
+                run_mma<kPair, false>(sm, L, tmem_base);
+        }
         __syncwarp();
     } else {
         run_epilogue<kMode, kPair>(sm, L, tmem_base);
@@ -906,6 +966,8 @@ cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int gri
     if (L.num_tiles <= 0 || grid <= 0) return cudaSuccess;
     // MI with the FP64 combine off runs the kernel without its code
     const int mode = (L.mode == kTcModeMI && !L.fixup) ? kTcModeMI32 : L.mode;
+    if (L.fp4 && (L.direct || (L.jobs == nullptr && L.job0.bn > kTcBNFp4)))
+        return cudaErrorInvalidValue;
     if (L.pair) {
         if (grid % 2 != 0 || L.direct) return cudaErrorInvalidValue;
         switch (mode) {

@@ -20,6 +20,13 @@ namespace gbmi {
 //    written and hold whatever the buffer held: every consumer masks them.  Any number of operands can share one
 //    buffer (each at its own first row), so one 2-D TMA descriptor of width
 //    128 bytes reaches every tile of every dataset.
+// P4 (the FP4 form of P, same buffer shape): for every block of 256 samples,
+//    one 128-byte row per variable holding two samples per byte as E2M1
+//    nibbles (0x0 / 0x2 = 1.0): samples 128 h + 16 g .. + 15 of the block
+//    (h = 0, 1; g = 0..7) are the 8 bytes at 64 h + 8 g, sample 2 k and 2 k + 1
+//    of those 16 in the low and high nibble of byte k.  k_blocks = m rounded up
+//    to 256, / 256.  A and B always share this order, so the Gram's dot
+//    products are the same sums as over samples in order.
 // Bp (popcount operand): one row per variable, bit (r % 32) of 32-bit word
 //    r / 32 holds sample r; wpr = ldp / 32 words per row, same row padding.
 // v  column counts, int32, one per variable.
@@ -31,6 +38,12 @@ constexpr int64_t kColPad = 128;
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t pack_rows(int64_t n) { return round_up(n, kRowPad); }
 inline int64_t pack_ld(int64_t m) { return round_up(m, kColPad); }
+// Samples per K block (one 128-byte operand row): 128 FP8, 256 FP4.
+constexpr int64_t kKbSamplesFp8 = 128;
+constexpr int64_t kKbSamplesFp4 = 256;
+inline int64_t kb_samples(bool fp4) { return fp4 ? kKbSamplesFp4 : kKbSamplesFp8; }
+// Padded sample count of an operand of either form.
+inline int64_t pack_ld_of(int64_t m, bool fp4) { return round_up(m, kb_samples(fp4)); }
 
 // Device error word bits (set by kernels whose bounded waits gave up).
 enum : uint32_t {
@@ -47,7 +60,7 @@ enum : uint32_t {
 struct PackJob {
     const uint8_t* X;    // m x n, leading dimension ldx
     int64_t m, n, ldx;
-    uint8_t* P;          // K-block-major FP8 operand (this job's first row), or null
+    uint8_t* P;          // K-block-major FP8 (or FP4) operand (this job's first row), or null
     uint32_t* Bp;        // bit-packed operand, rows_p x (ldp / 32) words, or null
     int32_t* v;          // column counts (zeroed before the launch), or null
     int64_t rows_p, ldp;
@@ -55,7 +68,7 @@ struct PackJob {
     int32_t gx;          // column blocks of 128 variables (rows_p / 128)
     int32_t tpc;         // 128-sample tiles walked by one CTA
     int32_t vec;         // 16-byte loads of X allowed
-    int32_t pad;
+    int32_t fp4;         // P is the FP4 form (ldp a multiple of 256)
 };
 // Fill the launch fields (gx, tpc, vec) of a job; returns its CTA count.
 // grouped: the job is one of many in a grouped launch (the most tiles per CTA).
@@ -134,7 +147,10 @@ cudaError_t launch_popcount(const PopcArgs& a, cudaStream_t s);
 // ------------------------------------------------------- tcgen05 FP8 Gram
 constexpr int kTcBM = 128;     // A rows per tile = TMEM lanes
 constexpr int kTcBNMax = 256;  // largest B rows per tile = accumulator columns
-constexpr int kTcBK = 128;     // samples (bytes) per pipeline stage = one operand row
+constexpr int kTcBK = 128;     // bytes per pipeline stage = one operand row
+// Widest tile of an FP4 launch: the block-scaled MMA reads its scale factors
+// from tensor memory, in the 16 columns each accumulator buffer leaves free.
+constexpr int kTcBNFp4 = 240;
 
 enum TcMode : int { kTcModeMI = 0, kTcModeCounts = 1, kTcModeCountsAdd = 2 };
 
@@ -143,10 +159,10 @@ struct GramJob {
     int64_t rowA, rowB;        // tensor-map row of (K block 0, variable 0) of A and B
     int64_t strideA, strideB;  // rows between consecutive K blocks (rows_p of A / B)
     int32_t k_begin;           // first K block accumulated by this launch
-    int32_t k_blocks;          // K blocks (k_blocks * 128 <= 2^24: exact FP32 counts)
+    int32_t k_blocks;          // K blocks (k_blocks * kb_samples <= 2^24: exact FP32 counts)
     int32_t n_a, n_b;          // valid variables of A and B
     int32_t symmetric;         // A == B: write (i, j) and (j, i) for j >= i only
-    int32_t bn;                // B rows per tile: 64, 128 or 256
+    int32_t bn;                // B rows per tile: 64, 128 or 256 (240 for FP4)
     int32_t pad;
     const MiVar* va;           // per-variable terms (MI mode)
     const MiVar* vb;
@@ -200,6 +216,11 @@ struct GramLaunch {
     // MI mode: 1 if any job has the FP64 combine on (then the kernel that
     // contains it is launched; else the one without it)
     int fixup;
+    // 1: the operands are the FP4 form (E2M1 nibbles, 256 samples per K
+    // block) and the Gram runs the block-scaled FP4 MMA (kind::mxf4, every
+    // scale factor 1.0): 0 and 1 are exact in E2M1, so the counts are the
+    // same integers.  Packed operands only; every job has bn <= 240.
+    int fp4;
 };
 
 // TMA descriptors of a K-block-major operand buffer of total_rows rows of 128

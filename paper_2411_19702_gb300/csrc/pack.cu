@@ -1,10 +1,11 @@
 // Pack pass: one read of X (m samples x n variables, row-major uint8) writes
 //   P  - the transposed FP8 operand of the tensor-core Gram in K-block-major
 //        order (for each block of 128 samples, one 128-byte row per variable;
-//        0x00 / 0x38 = E4M3 1.0 per sample), samples beyond m zeroed (they
-//        would add to every count); rows beyond n are not written (a garbage
-//        operand row only reaches accumulator rows or columns that every
-//        epilogue masks),
+//        0x00 / 0x38 = E4M3 1.0 per sample), or its FP4 form (for each block of
+//        256 samples, one 128-byte row of E2M1 nibbles 0x0 / 0x2), samples
+//        beyond m zeroed (they would add to every count); rows beyond n are
+//        not written (a garbage operand row only reaches accumulator rows or
+//        columns that every epilogue masks),
 //   Bp - the transposed bit-packed operand of the popcount Gram,
 //   v  - the column counts v_j = sum_r X_rj (Sec. 3.1, Term 2: v = D^T 1;
 //        also the diagonal of G11, Sec. 2 step 3).
@@ -81,166 +82,88 @@ __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
     return ((x * 0x01020408u) >> 24) & 0xFu;
 }
 
+// The four 0/1 bytes of x as four E2M1 nibbles (byte k -> nibble k, 1 -> 0x2
+// = 1.0, 0 -> 0x0), in the low 16 bits.
+__device__ __forceinline__ uint32_t bytes_to_e2m1(uint32_t x) {
+    return ((x & 0x1u) | ((x >> 4) & 0x10u) | ((x >> 8) & 0x100u) | ((x >> 12) & 0x1000u)) << 1;
+}
+
 // Thread layout of the transpose: warp w owns variables 16 w .. 16 w + 15 of
 // the CTA's 128 and all 128 samples of the tile; lane = 4 sg + vg takes the
 // 4 variables 16 w + 4 vg .. + 3 and the 16 samples 16 sg .. + 15.  A store
-// instruction of the warp then writes 4 whole 128-byte rows of P.  The tile
-// sits in shared memory with its 16-byte chunks XOR-swizzled by the row's
-// 16-row group (chunk ^ (r / 16) % 8), which keeps both the row-wise fill
-// and the column-wise reads of the transpose free of bank conflicts.
-template <bool kAligned>
-__device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, const int64_t by,
-                                         uint8_t* S, uint8_t* raw) {
+// instruction of the warp then writes 4 whole 128-byte rows of P (4 half rows
+// of 64 bytes in the FP4 form).  The tile sits in shared memory with its
+// 16-byte chunks XOR-swizzled by the row's 16-row group (chunk ^ (r / 16) % 8),
+// which keeps both the row-wise fill and the column-wise reads of the
+// transpose free of bank conflicts.
+__device__ __forceinline__ int swz_chunk(int r, int chunk) { return chunk ^ ((r >> 4) & 7); }
+
+// Transpose the tile in S (128 samples from r0, 128 variables from j0), add
+// its column sums to colsum and store this thread's pieces of P and Bp.
+__device__ __forceinline__ void transpose_store(const PackJob& a, const uint8_t* S, int64_t tile,
+                                                int64_t j0, int (&colsum)[4]) {
     const int t = threadIdx.x;
     const int w = t >> 5;
     const int lane = t & 31;
     const int vg = lane & 3;
     const int sg = lane >> 2;
     const int colw = 4 * w + vg;   // word column (4 variables) of this thread
-    const int64_t j0 = bx * kTileJ;
-    const int64_t tiles_total = a.ldp / kTileR;
-    const int64_t tile_begin = by * a.tpc;
-    const int64_t tile_end = min(tile_begin + a.tpc, tiles_total);
-    const bool vec = a.vec != 0;
-
-    int colsum[4] = {0, 0, 0, 0};
     const uint32_t* S32 = reinterpret_cast<const uint32_t*>(S);
-
-    // The next tile's loads are issued before the current tile is transposed
-    // and stored, so they are in flight during that work.  Aligned rows: one
-    // 16-byte load per lane and row, into registers.  Rows of X that are not
-    // 16-byte aligned: the aligned granules covering each row's 128-byte slice
-    // (lane l of the row's 8 lanes copies granule l, lane 7 also granule 8)
-    // go to this warp's raw rows in shared memory by cp.async, copying only
-    // bytes of [j0, min(j0 + 128, n)) of the row and zero-filling the rest; the
-    // realignment (5 word reads and 4 funnel shifts per lane and row) happens
-    // when the tile is written to S, so no registers hold the loads meanwhile.
-    uint4 pre[4];
-    // unaligned rows: this warp's raw rows, the lane's row among the warp's 4 per
-    // quarter, and its granule
-    auto wraw = [&] { return raw + (t >> 5) * kRawWarpBytes; };
-    const int rr_w = (t >> 3) & 3;
-    const int gl = t & 7;
-    auto issue_tile = [&](int64_t tile) {
-        const int64_t r0 = tile * kTileR;
-        if constexpr (kAligned) {
-            const int64_t jl = j0 + (t & 7) * 16;
+    const int swz = colw ^ (4 * sg);   // rows 16 sg .. +15 share one swizzle
+    uint32_t col[4][4];   // col[c][g]: variable 16 w + 4 vg + c, samples 16 sg + 4 g .. +3
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t r = r0 + q * 32 + (t >> 3);
-                pre[q] = make_uint4(0, 0, 0, 0);
-                if (r < a.m && jl < a.n)
-                    pre[q] = __ldg(reinterpret_cast<const uint4*>(a.X + r * a.ldx + jl));
-            }
-        } else {
-            const int64_t keep_row = a.n - j0 < kTileJ ? a.n - j0 : kTileJ;   // >= 1
+    for (int g = 0; g < 4; ++g) {
+        const int rr = sg * 16 + g * 4;
+        const uint32_t w0 = nz_bytes(S32[(rr + 0) * (kTileJ / 4) + swz]);
+        const uint32_t w1 = nz_bytes(S32[(rr + 1) * (kTileJ / 4) + swz]);
+        const uint32_t w2 = nz_bytes(S32[(rr + 2) * (kTileJ / 4) + swz]);
+        const uint32_t w3 = nz_bytes(S32[(rr + 3) * (kTileJ / 4) + swz]);
+        // column sums: bytes of w0+w1+w2+w3 are per-variable counts (<= 4)
+        const uint32_t s4 = w0 + w1 + w2 + w3;
+        colsum[0] += s4 & 0xFF;
+        colsum[1] += (s4 >> 8) & 0xFF;
+        colsum[2] += (s4 >> 16) & 0xFF;
+        colsum[3] += s4 >> 24;
+        transpose4x4(w0, w1, w2, w3, col[0][g], col[1][g], col[2][g], col[3][g]);
+    }
+    const int64_t rbase = tile * kTileR + sg * 16;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t r = r0 + q * 32 + (t >> 3);
-                const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(
-                    wraw() + (4 * q + rr_w) * kRawRowBytes + 16 * gl));
-                if (r < a.m) {
-                    const uintptr_t ad = reinterpret_cast<uintptr_t>(a.X + r * a.ldx + j0);
-                    const int sft = static_cast<int>(ad & 15);
-                    const uint8_t* G = reinterpret_cast<const uint8_t*>(ad - sft);
-                    // valid bytes of granule k: [sft, sft + keep_row) in the row's granules
-                    const int64_t end = sft + keep_row;
-                    const int64_t n0 = end - 16 * gl;
-                    cp_async16(dst, G + 16 * gl,
-                               static_cast<uint32_t>(n0 <= 0 ? 0 : (n0 > 16 ? 16 : n0)));
-                    if (gl == 7) {
-                        const int64_t n8 = end - 128;
-                        cp_async16(dst + 16, G + 128,
-                                   static_cast<uint32_t>(n8 <= 0 ? 0 : (n8 > 16 ? 16 : n8)));
-                    }
-                } else {   // samples beyond m: zeros
-                    cp_async16(dst, a.X, 0u);
-                    if (gl == 7) cp_async16(dst + 16, a.X, 0u);
-                }
-            }
-            cp_async_commit();
+    for (int c = 0; c < 4; ++c) {
+        const int64_t j = j0 + colw * 4 + c;
+        if (j >= a.n) continue;   // padding rows are left as they are: masked downstream
+        if (a.P != nullptr && a.fp4) {
+            // 256-sample K block tile / 2, half tile % 2: 64 bytes per variable
+            uint2 o;
+            o.x = bytes_to_e2m1(col[c][0]) | (bytes_to_e2m1(col[c][1]) << 16);
+            o.y = bytes_to_e2m1(col[c][2]) | (bytes_to_e2m1(col[c][3]) << 16);
+            *reinterpret_cast<uint2*>(a.P + ((tile >> 1) * a.rows_p + j) * kTileR +
+                                      (tile & 1) * (kTileR / 2) + sg * 8) = o;
+        } else if (a.P != nullptr) {
+            uint4 o;
+            o.x = col[c][0] * 0x38u;
+            o.y = col[c][1] * 0x38u;
+            o.z = col[c][2] * 0x38u;
+            o.w = col[c][3] * 0x38u;
+            *reinterpret_cast<uint4*>(a.P + (tile * a.rows_p + j) * kTileR + sg * 16) = o;
         }
-    };
-    if (tile_begin < tile_end) issue_tile(tile_begin);
-
-    for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
-        const int64_t r0 = tile * kTileR;
-        if constexpr (!kAligned) {
-            // this tile's raw rows have landed (the warp's own copies) -> realign
-            cp_async_wait_all();
-            __syncwarp();
-            const uint32_t* wr = reinterpret_cast<const uint32_t*>(wraw());
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t r = r0 + q * 32 + (t >> 3);
-                const int sft = r < a.m ? static_cast<int>(reinterpret_cast<uintptr_t>(
-                                                               a.X + r * a.ldx + j0) & 15)
-                                        : 0;
-                const uint32_t* row = wr + (4 * q + rr_w) * (kRawRowBytes / 4) + (sft >> 2) +
-                                      4 * gl;
-                const uint32_t sh = static_cast<uint32_t>(sft & 3) * 8u;
-                const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3], w4 = row[4];
-                pre[q] = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
-                                    __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
-            }
-            __syncwarp();   // the raw rows are refilled by the next issue
-        }
-        // ---- 128 samples x 128 variables into S (row r, swizzled 16-byte chunks)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int r = q * 32 + (t >> 3);
-            const int chunk = (t & 7) ^ ((r >> 4) & 7);
-            *reinterpret_cast<uint4*>(S + r * kTileJ + chunk * 16) = pre[q];
-        }
-        __syncthreads();
-        if (tile + 1 < tile_end) issue_tile(tile + 1);
-
-        // ---- transpose: variables 16 w + 4 vg .. +3, samples 16 sg .. +15
-        const int swz = colw ^ (4 * sg);   // rows 16 sg .. +15 share one swizzle
-        uint32_t col[4][4];   // col[c][g]: variable 16 w + 4 vg + c, samples 16 sg + 4 g .. +3
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const int rr = sg * 16 + g * 4;
-            const uint32_t w0 = nz_bytes(S32[(rr + 0) * (kTileJ / 4) + swz]);
-            const uint32_t w1 = nz_bytes(S32[(rr + 1) * (kTileJ / 4) + swz]);
-            const uint32_t w2 = nz_bytes(S32[(rr + 2) * (kTileJ / 4) + swz]);
-            const uint32_t w3 = nz_bytes(S32[(rr + 3) * (kTileJ / 4) + swz]);
-            // column sums: bytes of w0+w1+w2+w3 are per-variable counts (<= 4)
-            const uint32_t s4 = w0 + w1 + w2 + w3;
-            colsum[0] += s4 & 0xFF;
-            colsum[1] += (s4 >> 8) & 0xFF;
-            colsum[2] += (s4 >> 16) & 0xFF;
-            colsum[3] += s4 >> 24;
-            transpose4x4(w0, w1, w2, w3, col[0][g], col[1][g], col[2][g], col[3][g]);
-        }
-        __syncthreads();   // S is rewritten by the next tile
-
-        const int64_t rbase = r0 + sg * 16;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int64_t j = j0 + colw * 4 + c;
-            if (j >= a.n) continue;   // padding rows are left as they are: masked downstream
-            if (a.P != nullptr) {
-                uint4 o;
-                o.x = col[c][0] * 0x38u;
-                o.y = col[c][1] * 0x38u;
-                o.z = col[c][2] * 0x38u;
-                o.w = col[c][3] * 0x38u;
-                *reinterpret_cast<uint4*>(a.P + (tile * a.rows_p + j) * kTileR + sg * 16) = o;
-            }
-            if (a.Bp != nullptr) {
-                const uint32_t bits = bytes_to_nibble(col[c][0]) |
-                                      (bytes_to_nibble(col[c][1]) << 4) |
-                                      (bytes_to_nibble(col[c][2]) << 8) |
-                                      (bytes_to_nibble(col[c][3]) << 12);
-                uint16_t* B16 = reinterpret_cast<uint16_t*>(a.Bp);
-                B16[j * (a.ldp / 16) + rbase / 16] = static_cast<uint16_t>(bits);
-            }
+        if (a.Bp != nullptr) {
+            const uint32_t bits = bytes_to_nibble(col[c][0]) |
+                                  (bytes_to_nibble(col[c][1]) << 4) |
+                                  (bytes_to_nibble(col[c][2]) << 8) |
+                                  (bytes_to_nibble(col[c][3]) << 12);
+            uint16_t* B16 = reinterpret_cast<uint16_t*>(a.Bp);
+            B16[j * (a.ldp / 16) + rbase / 16] = static_cast<uint16_t>(bits);
         }
     }
+}
 
+// Column sums of the CTA's variables: sum over the 8 sample groups of the warp
+// (lane bits 2-4), one atomic add per variable.
+__device__ __forceinline__ void flush_colsum(const PackJob& a, int64_t j0, const int (&colsum)[4]) {
     if (a.v == nullptr) return;
-    // sum over the 8 sample groups of the warp (lane bits 2-4), one add per variable
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int colw = 4 * (t >> 5) + (lane & 3);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int x = colsum[c];
@@ -248,25 +171,165 @@ __device__ __forceinline__ void pack_cta(const PackJob& a, const int64_t bx, con
         x += __shfl_xor_sync(0xffffffffu, x, 8);
         x += __shfl_xor_sync(0xffffffffu, x, 16);
         const int64_t j = j0 + colw * 4 + c;
-        if (sg == 0 && j < a.n && x != 0) atomicAdd(a.v + j, x);
+        if ((lane >> 2) == 0 && j < a.n && x != 0) atomicAdd(a.v + j, x);
     }
 }
+
+// Rows that are 16-byte aligned: each tile is copied straight into its
+// swizzled shared-memory slot by cp.async (lane l of a row's 8 lanes copies
+// its 16-byte chunk; bytes outside [0, m) x [0, n) are zero-filled), in a ring
+// of kStagesA tiles, so kStagesA - 1 tiles' loads are in flight while one is
+// transposed and no registers hold them.
+constexpr int kStagesA = 3;
+constexpr int kTileBytes = kTileR * kTileJ;
+
+__device__ __forceinline__ void pack_cta_aligned(const PackJob& a, const int64_t bx,
+                                                 const int64_t by, uint8_t* S) {
+    const int t = threadIdx.x;
+    const int64_t j0 = bx * kTileJ;
+    const int64_t tiles_total = a.ldp / kTileR;
+    const int64_t tile_begin = by * a.tpc;
+    const int64_t tile_end = min(tile_begin + a.tpc, tiles_total);
+    const int64_t jl = j0 + (t & 7) * 16;
+    auto issue = [&](int64_t tile, uint8_t* Sb) {
+        if (tile < tile_end) {
+            const int64_t r0 = tile * kTileR;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = q * 32 + (t >> 3);
+                const int64_t rg = r0 + r;
+                const bool in = rg < a.m && jl < a.n;
+                const uint32_t dst = static_cast<uint32_t>(
+                    __cvta_generic_to_shared(Sb + r * kTileJ + swz_chunk(r, t & 7) * 16));
+                cp_async16(dst, in ? a.X + rg * a.ldx + jl : a.X, in ? 16u : 0u);
+            }
+        }
+        cp_async_commit();   // one group per tile slot, empty past the end
+    };
+#pragma unroll
+    for (int s = 0; s < kStagesA - 1; ++s) issue(tile_begin + s, S + s * kTileBytes);
+    int colsum[4] = {0, 0, 0, 0};
+    int slot = 0;
+    for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
+        // this thread's copies of `tile` have landed, then everyone's; every
+        // thread is also done with the slot the next issue refills
+        asm volatile("cp.async.wait_group %0;" ::"n"(kStagesA - 2) : "memory");
+        __syncthreads();
+        const int refill = slot == 0 ? kStagesA - 1 : slot - 1;
+        issue(tile + kStagesA - 1, S + refill * kTileBytes);
+        transpose_store(a, S + slot * kTileBytes, tile, j0, colsum);
+        slot = slot + 1 == kStagesA ? 0 : slot + 1;
+    }
+    cp_async_wait_all();
+    flush_colsum(a, j0, colsum);
+}
+
+// Rows that are not 16-byte aligned: every warp stages its 16 rows of a tile
+// (4 per quarter) in its raw rows by cp.async, as the aligned granules that
+// cover each row's 128-byte slice (lane l of the row's 8 lanes copies granule
+// l, lane 7 also granule 8), copying only bytes of [j0, min(j0 + 128, n)) of
+// the row and zero-filling the rest; the next tile's copies are in flight
+// while the current one is transposed.  The realignment (5 word reads and 4
+// funnel shifts per lane and row) happens when the tile is written to S.
+__device__ __forceinline__ void pack_cta_unaligned(const PackJob& a, const int64_t bx,
+                                                   const int64_t by, uint8_t* S, uint8_t* raw) {
+    const int t = threadIdx.x;
+    const int64_t j0 = bx * kTileJ;
+    const int64_t tiles_total = a.ldp / kTileR;
+    const int64_t tile_begin = by * a.tpc;
+    const int64_t tile_end = min(tile_begin + a.tpc, tiles_total);
+    uint8_t* const wraw = raw + (t >> 5) * kRawWarpBytes;   // this warp's raw rows
+    const int rr_w = (t >> 3) & 3;   // the lane's row among the warp's 4 per quarter
+    const int gl = t & 7;            // and its granule
+    auto issue_tile = [&](int64_t tile) {
+        const int64_t r0 = tile * kTileR;
+        const int64_t keep_row = a.n - j0 < kTileJ ? a.n - j0 : kTileJ;   // >= 1
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t r = r0 + q * 32 + (t >> 3);
+            const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(
+                wraw + (4 * q + rr_w) * kRawRowBytes + 16 * gl));
+            if (r < a.m) {
+                const uintptr_t ad = reinterpret_cast<uintptr_t>(a.X + r * a.ldx + j0);
+                const int sft = static_cast<int>(ad & 15);
+                const uint8_t* G = reinterpret_cast<const uint8_t*>(ad - sft);
+                // valid bytes of granule k: [sft, sft + keep_row) in the row's granules
+                const int64_t end = sft + keep_row;
+                const int64_t n0 = end - 16 * gl;
+                cp_async16(dst, G + 16 * gl,
+                           static_cast<uint32_t>(n0 <= 0 ? 0 : (n0 > 16 ? 16 : n0)));
+                if (gl == 7) {
+                    const int64_t n8 = end - 128;
+                    cp_async16(dst + 16, G + 128,
+                               static_cast<uint32_t>(n8 <= 0 ? 0 : (n8 > 16 ? 16 : n8)));
+                }
+            } else {   // samples beyond m: zeros
+                cp_async16(dst, a.X, 0u);
+                if (gl == 7) cp_async16(dst + 16, a.X, 0u);
+            }
+        }
+        cp_async_commit();
+    };
+    if (tile_begin < tile_end) issue_tile(tile_begin);
+
+    int colsum[4] = {0, 0, 0, 0};
+    for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
+        const int64_t r0 = tile * kTileR;
+        // this tile's raw rows have landed (the warp's own copies) -> realign
+        cp_async_wait_all();
+        __syncwarp();
+        const uint32_t* wr = reinterpret_cast<const uint32_t*>(wraw);
+        uint4 pre[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t r = r0 + q * 32 + (t >> 3);
+            const int sft = r < a.m ? static_cast<int>(reinterpret_cast<uintptr_t>(
+                                                           a.X + r * a.ldx + j0) & 15)
+                                    : 0;
+            const uint32_t* row = wr + (4 * q + rr_w) * (kRawRowBytes / 4) + (sft >> 2) + 4 * gl;
+            const uint32_t sh = static_cast<uint32_t>(sft & 3) * 8u;
+            const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3], w4 = row[4];
+            pre[q] = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                                __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+        }
+        __syncwarp();   // the raw rows are refilled by the next issue
+        // ---- 128 samples x 128 variables into S (row r, swizzled 16-byte chunks)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = q * 32 + (t >> 3);
+            *reinterpret_cast<uint4*>(S + r * kTileJ + swz_chunk(r, t & 7) * 16) = pre[q];
+        }
+        __syncthreads();
+        if (tile + 1 < tile_end) issue_tile(tile + 1);
+        transpose_store(a, S, tile, j0, colsum);
+        __syncthreads();   // S is rewritten by the next tile
+    }
+    flush_colsum(a, j0, colsum);
+}
+
+// Shared memory of a pack CTA: the aligned ring (kStagesA tiles) or one tile
+// plus the warps' raw rows, whichever is larger.
+constexpr int kPackSmem = kStagesA * kTileBytes > kTileBytes + (kPackThreads / 32) * kRawWarpBytes
+                              ? kStagesA * kTileBytes
+                              : kTileBytes + (kPackThreads / 32) * kRawWarpBytes;
+static_assert(kPackSmem <= 48 * 1024, "static shared memory of a pack CTA");
 
 // One instantiation for 16-byte aligned rows, one for the rest.
 template <bool kAligned>
 __global__ void __launch_bounds__(kPackThreads, 4)   // 4 CTAs per SM: loads in flight
 pack_kernel(const PackJob job) {
-    __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
-    __shared__ __align__(16) uint8_t R[kAligned ? 16 : (kPackThreads / 32) * kRawWarpBytes];
+    __shared__ __align__(128) uint8_t smem[kAligned ? kStagesA * kTileBytes : kPackSmem];
     const int64_t c = blockIdx.x;
-    pack_cta<kAligned>(job, c % job.gx, c / job.gx, S, R);
+    if constexpr (kAligned)
+        pack_cta_aligned(job, c % job.gx, c / job.gx, smem);
+    else
+        pack_cta_unaligned(job, c % job.gx, c / job.gx, smem, smem + kTileBytes);
 }
 
 __global__ void __launch_bounds__(kPackThreads, 4)
 pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs,
                     const int32_t* __restrict__ cta_job) {
-    __shared__ __align__(16) uint8_t S[kTileR * kTileJ];
-    __shared__ __align__(16) uint8_t R[(kPackThreads / 32) * kRawWarpBytes];
+    __shared__ __align__(128) uint8_t smem[kPackSmem];
     const int64_t c = blockIdx.x;
     int lo = 0, hi = njobs - 1;   // last job whose cta_begin <= c
     if (cta_job != nullptr) {
@@ -280,9 +343,9 @@ pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs,
     const PackJob job = jobs[lo];
     const int64_t cl = c - job.cta_begin;
     if (job.vec)
-        pack_cta<true>(job, cl % job.gx, cl / job.gx, S, R);
+        pack_cta_aligned(job, cl % job.gx, cl / job.gx, smem);
     else
-        pack_cta<false>(job, cl % job.gx, cl / job.gx, S, R);
+        pack_cta_unaligned(job, cl % job.gx, cl / job.gx, smem, smem + kTileBytes);
 }
 
 __global__ void validate_kernel(const uint8_t* X, int64_t m, int64_t n, int64_t ldx,
@@ -391,6 +454,7 @@ int64_t pack_job_ctas(PackJob& a, bool grouped) {
 
 cudaError_t launch_pack(const PackJob& job, cudaStream_t s) {
     if (job.rows_p % kTileJ != 0 || job.ldp % kTileR != 0) return cudaErrorInvalidValue;
+    if (job.fp4 && job.ldp % (2 * kTileR) != 0) return cudaErrorInvalidValue;
     PackJob j = job;
     const int64_t ctas = pack_job_ctas(j);
     if (ctas <= 0 || ctas > 0x7FFFFFFF) return cudaErrorInvalidValue;

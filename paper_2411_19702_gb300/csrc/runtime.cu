@@ -31,7 +31,7 @@ bool log_errors() {
 }
 
 // Option defaults from the environment (GBMI_FIXUP, GBMI_TILE_N, GBMI_PAIR,
-// GBMI_DIRECT, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS), read once
+// GBMI_DIRECT, GBMI_FP4, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS), read once
 // when the library loads; values out of range are ignored.
 struct EnvOptions {
     EnvOptions() {
@@ -53,6 +53,7 @@ struct EnvOptions {
             g_opt.tile_n = static_cast<int>(v);
         if (num("GBMI_PAIR", 0, 2, &v)) g_opt.pair = static_cast<int>(v);
         if (num("GBMI_DIRECT", 0, 1, &v)) g_opt.direct = static_cast<int>(v);
+        if (num("GBMI_FP4", 0, 1, &v)) g_opt.fp4 = static_cast<int>(v);
         if (num("GBMI_TIMEOUT_NS", 1000, 600000000000LL, &v))
             g_opt.timeout_ns = static_cast<uint64_t>(v);
         if (num("GBMI_GROUP_COLS", 1, 1 << 20, &v)) g_opt.group_cols = static_cast<int>(v);

@@ -34,6 +34,7 @@ struct Options {
     int pair = 1;                        // 1: CTA-pair (cta_group::2) Gram where it fills the GPU
     int csr_path = 0;                    // CSR input: 0 cost model, 1 pair enumeration, 2 dense
     int split_k = 0;                     // sample split of few-tile Grams: 0 auto, 1 off, 2 forced
+    int fp4 = 1;                         // tensor-core operands in the FP4 form (block-scaled MMA)
 };
 
 struct DeviceCtx {

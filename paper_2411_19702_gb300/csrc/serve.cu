@@ -2,8 +2,9 @@
 // (see gbmi_server_* in gbmi.h).
 //
 // Memory: one device arena of the budget, sub-allocated first-fit in 256-byte
-// units.  A dataset owns a packed-operand region (K-block-major FP8 rows of
-// 128 samples, so the arena's TMA descriptors reach every dataset) and a
+// units.  A dataset owns a packed-operand region (K-block-major rows of 128
+// bytes, FP4 or FP8 as GBMI_OPT_FP4 was when the server was created, so the
+// arena's TMA descriptors reach every dataset) and a
 // region for its column counts and per-variable terms; a request owns its
 // output.  Admission is by memory: a queued request is admitted when its
 // output, and the regions of any dataset it needs that is not yet resident,
@@ -127,6 +128,7 @@ struct gbmi_server {
     int sm_count = 0;
     int pair_clusters = 0;
     int max_batch = 64;
+    bool fp4 = false;   // datasets packed in the FP4 form (GBMI_OPT_FP4 at creation)
     gbmi::rt::DevBuf mem;
     gbmi::Arena arena;
     gbmi::OperandMaps maps;
@@ -229,7 +231,8 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
         j.P = at(S, d.off_p);
         j.v = v_of(S, d);
         j.rows_p = d.rows_p;
-        j.ldp = d.kb * kTcBK;
+        j.ldp = d.kb * kb_samples(S->fp4);
+        j.fp4 = S->fp4 ? 1 : 0;
         j.cta_begin = ctas;
         ctas += pack_job_ctas(j);
         pj.push_back(j);
@@ -242,6 +245,7 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
     // requests whose both sides span at least 768 variables run on CTA pairs
     constexpr int64_t kPairMinN = 768;
     const bool pairs_ok = rt::g_opt.pair != 0 && S->pair_clusters > 0 && rt::g_opt.tile_n == 0;
+    const int bn_max = S->fp4 ? kTcBNFp4 : kTcBNMax;
     for (int64_t t : tickets) {
         const Request& r = S->reqs[t];
         const Dataset& da = S->datasets[r.a];
@@ -260,7 +264,7 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
         g.symmetric = sym ? 1 : 0;
         {
             std::lock_guard<std::recursive_mutex> lk(rt::g_mu);
-            g.bn = rt::choose_bn(r.m, r.n_a, r.n_b, sym);
+            g.bn = std::min(rt::choose_bn(r.m, r.n_a, r.n_b, sym), bn_max);
         }
         g.va = vars_of(S, da);
         g.vb = vars_of(S, db);
@@ -269,7 +273,7 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
         g.mp = rt::mi_params_plain(r.m, 0, nullptr);
         const bool pj =
             pairs_ok && (rt::g_opt.pair == 2 || (r.n_a >= kPairMinN && r.n_b >= kPairMinN));
-        if (pj) g.bn = kTcBNMax;
+        if (pj) g.bn = bn_max;
         gj.push_back(g);
         pair_job.push_back(pj ? 1 : 0);
         const int64_t nt = gram_tile_count(r.n_a, r.n_b, g.bn, sym, pj ? 2 * kTcBM : kTcBM);
@@ -330,6 +334,7 @@ gbmi_status launch_batch(gbmi_server* S, int k, const std::vector<int64_t>& tick
     std::memset(&L, 0, sizeof(L));
     L.jobs = static_cast<const GramJob*>(sl.djobs.p);
     L.mode = kTcModeMI;
+    L.fp4 = S->fp4 ? 1 : 0;
     L.err = ctrl + 1;
     L.timeout_ns = rt::g_opt.timeout_ns;
     uint64_t launches = sl.packs.size() + (sl.packs.empty() ? 0 : 1);
@@ -499,6 +504,7 @@ gbmi_status create(int64_t budget, int max_batch, gbmi_server** out) {
     S->max_batch = max_batch;
     S->sm_count = cp->sm_count;
     S->pair_clusters = cp->pair_clusters;
+    S->fp4 = rt::g_opt.fp4 != 0;
     cudaGetDevice(&S->device);
     const size_t bytes = static_cast<size_t>(budget) & ~static_cast<size_t>(255);
     gbmi_status st = rt::ensure(S->mem, bytes, "server arena");
@@ -546,7 +552,7 @@ gbmi_status gbmi_server_add_dataset(gbmi_server* S, const uint8_t* X, int64_t m,
     d.X = X;
     d.m = m;
     d.n = n;
-    d.kb = pack_ld(m) / kTcBK;
+    d.kb = pack_ld_of(m, S->fp4) / kb_samples(S->fp4);
     d.rows_p = pack_rows(n);
     *id = S->next_ds++;
     S->datasets[*id] = d;

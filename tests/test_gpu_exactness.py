@@ -1,10 +1,12 @@
 """Exact counts at the accumulation limits, and the bounded device-side waits.
 
-FP32 accumulation of 0/1 FP8 products is exact while a count stays at most
-2^24; one Gram launch therefore accumulates at most 2^24 samples, the plain
-path adds launch results in int32, and the fused path adds the earlier
+FP32 accumulation of 0/1 FP4 or FP8 products is exact while a count stays at
+most 2^24; one Gram launch therefore accumulates at most 2^24 samples, the
+plain path adds launch results in int32, and the fused path adds the earlier
 chunks' int32 counts to its last launch's accumulator.  All-ones columns
 make every accumulator reach m, the largest value it can hold for that m.
+Every test runs with both operand forms (FP4: 256 samples per K block; FP8:
+128).
 """
 from __future__ import annotations
 
@@ -17,6 +19,13 @@ import oracle  # noqa: E402
 from paper_2411_19702_gb300 import gbmi  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, params=[1, 0], ids=["fp4", "fp8"])
+def _operand_form(request):
+    gbmi.set_option(gbmi.OPT_FP4, request.param)
+    yield request.param
+    gbmi.set_option(gbmi.OPT_FP4, 1)
 
 
 @pytest.fixture(autouse=True)

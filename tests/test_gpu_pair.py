@@ -1,6 +1,7 @@
 """CTA-pair Gram: clusters of two SMs sharing one tcgen05 cta_group::2 MMA.
 
-The pair kernel computes 256 x 256 tiles (each SM stages half of A and half
+The pair kernel computes 256 x 256 tiles (256 x 240 with FP4 operands; each
+SM stages half of A and half
 of B; CTA 0 loads both halves and issues the MMAs, both CTAs run the
 epilogue on their half of the accumulator).  Counts must be bit-exact
 (against the oracle and the popcount path, up to 2^24 samples per launch and
@@ -37,6 +38,14 @@ def _single(fn, *a, **k):
         return out
     finally:
         gbmi.set_option(gbmi.OPT_PAIR, 2)
+
+
+@pytest.fixture(autouse=True, params=[1, 0], ids=["fp4", "fp8"])
+def _operand_form(request):
+    """Both operand forms: FP4 (256 x 240 pair tiles) and FP8 (256 x 256)."""
+    gbmi.set_option(gbmi.OPT_FP4, request.param)
+    yield request.param
+    gbmi.set_option(gbmi.OPT_FP4, 1)
 
 
 @pytest.fixture(scope="module", autouse=True)
