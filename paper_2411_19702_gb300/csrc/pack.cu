@@ -82,12 +82,6 @@ __device__ __forceinline__ uint32_t bytes_to_nibble(uint32_t x) {
     return ((x * 0x01020408u) >> 24) & 0xFu;
 }
 
-// The four 0/1 bytes of x as four E2M1 nibbles (byte k -> nibble k, 1 -> 0x2
-// = 1.0, 0 -> 0x0), in the low 16 bits.
-__device__ __forceinline__ uint32_t bytes_to_e2m1(uint32_t x) {
-    return ((x & 0x1u) | ((x >> 4) & 0x10u) | ((x >> 8) & 0x100u) | ((x >> 12) & 0x1000u)) << 1;
-}
-
 // Thread layout of the transpose: warp w owns variables 16 w .. 16 w + 15 of
 // the CTA's 128 and all 128 samples of the tile; lane = 4 sg + vg takes the
 // 4 variables 16 w + 4 vg .. + 3 and the 16 samples 16 sg .. + 15.  A store
@@ -100,6 +94,10 @@ __device__ __forceinline__ int swz_chunk(int r, int chunk) { return chunk ^ ((r 
 
 // Transpose the tile in S (128 samples from r0, 128 variables from j0), add
 // its column sums to colsum and store this thread's pieces of P and Bp.
+// The pack is bound by instruction issue more than by HBM, so the FP4 form
+// skips the byte transpose: the E2M1 byte of samples (2k, 2k + 1) of the four
+// variables of a word column is (w_2k << 1) | (w_2k+1 << 5) of the 0/1 sample
+// words, and two byte permutes per four samples regroup them by variable.
 __device__ __forceinline__ void transpose_store(const PackJob& a, const uint8_t* S, int64_t tile,
                                                 int64_t j0, int (&colsum)[4]) {
     const int t = threadIdx.x;
@@ -110,51 +108,73 @@ __device__ __forceinline__ void transpose_store(const PackJob& a, const uint8_t*
     const int colw = 4 * w + vg;   // word column (4 variables) of this thread
     const uint32_t* S32 = reinterpret_cast<const uint32_t*>(S);
     const int swz = colw ^ (4 * sg);   // rows 16 sg .. +15 share one swizzle
-    uint32_t col[4][4];   // col[c][g]: variable 16 w + 4 vg + c, samples 16 sg + 4 g .. +3
+    const int64_t jw = j0 + colw * 4;  // first of the thread's 4 variables
+    uint32_t acc4 = 0;   // byte c: this tile's count of variable jw + c (<= 16)
+    if (a.fp4 && a.Bp == nullptr) {
+        uint32_t v01[4], v23[4];   // per 4 samples: variables 0, 1 and 2, 3 (16 bits each)
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const int rr = sg * 16 + g * 4;
-        const uint32_t w0 = nz_bytes(S32[(rr + 0) * (kTileJ / 4) + swz]);
-        const uint32_t w1 = nz_bytes(S32[(rr + 1) * (kTileJ / 4) + swz]);
-        const uint32_t w2 = nz_bytes(S32[(rr + 2) * (kTileJ / 4) + swz]);
-        const uint32_t w3 = nz_bytes(S32[(rr + 3) * (kTileJ / 4) + swz]);
-        // column sums: bytes of w0+w1+w2+w3 are per-variable counts (<= 4)
-        const uint32_t s4 = w0 + w1 + w2 + w3;
-        colsum[0] += s4 & 0xFF;
-        colsum[1] += (s4 >> 8) & 0xFF;
-        colsum[2] += (s4 >> 16) & 0xFF;
-        colsum[3] += s4 >> 24;
-        transpose4x4(w0, w1, w2, w3, col[0][g], col[1][g], col[2][g], col[3][g]);
-    }
-    const int64_t rbase = tile * kTileR + sg * 16;
+        for (int g = 0; g < 4; ++g) {
+            const int rr = sg * 16 + g * 4;
+            const uint32_t w0 = nz_bytes(S32[(rr + 0) * (kTileJ / 4) + swz]);
+            const uint32_t w1 = nz_bytes(S32[(rr + 1) * (kTileJ / 4) + swz]);
+            const uint32_t w2 = nz_bytes(S32[(rr + 2) * (kTileJ / 4) + swz]);
+            const uint32_t w3 = nz_bytes(S32[(rr + 3) * (kTileJ / 4) + swz]);
+            acc4 += (w0 + w1) + (w2 + w3);
+            const uint32_t A = (w0 << 1) | (w1 << 5);   // byte c: samples 0, 1 of variable c
+            const uint32_t B = (w2 << 1) | (w3 << 5);   // samples 2, 3
+            v01[g] = __byte_perm(A, B, 0x5140);
+            v23[g] = __byte_perm(A, B, 0x7362);
+        }
+        // variable c: samples 16 sg .. + 15 as 8 bytes (64 h + 8 sg of its K-block row)
+        const uint2 o[4] = {
+            make_uint2(__byte_perm(v01[0], v01[1], 0x5410), __byte_perm(v01[2], v01[3], 0x5410)),
+            make_uint2(__byte_perm(v01[0], v01[1], 0x7632), __byte_perm(v01[2], v01[3], 0x7632)),
+            make_uint2(__byte_perm(v23[0], v23[1], 0x5410), __byte_perm(v23[2], v23[3], 0x5410)),
+            make_uint2(__byte_perm(v23[0], v23[1], 0x7632), __byte_perm(v23[2], v23[3], 0x7632))};
+        uint8_t* const dst = a.P + ((tile >> 1) * a.rows_p + jw) * kTileR +
+                             (tile & 1) * (kTileR / 2) + sg * 8;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int64_t j = j0 + colw * 4 + c;
-        if (j >= a.n) continue;   // padding rows are left as they are: masked downstream
-        if (a.P != nullptr && a.fp4) {
-            // 256-sample K block tile / 2, half tile % 2: 64 bytes per variable
-            uint2 o;
-            o.x = bytes_to_e2m1(col[c][0]) | (bytes_to_e2m1(col[c][1]) << 16);
-            o.y = bytes_to_e2m1(col[c][2]) | (bytes_to_e2m1(col[c][3]) << 16);
-            *reinterpret_cast<uint2*>(a.P + ((tile >> 1) * a.rows_p + j) * kTileR +
-                                      (tile & 1) * (kTileR / 2) + sg * 8) = o;
-        } else if (a.P != nullptr) {
-            uint4 o;
-            o.x = col[c][0] * 0x38u;
-            o.y = col[c][1] * 0x38u;
-            o.z = col[c][2] * 0x38u;
-            o.w = col[c][3] * 0x38u;
-            *reinterpret_cast<uint4*>(a.P + (tile * a.rows_p + j) * kTileR + sg * 16) = o;
+        for (int c = 0; c < 4; ++c)   // padding rows are left as they are: masked downstream
+            if (jw + c < a.n) *reinterpret_cast<uint2*>(dst + c * kTileR) = o[c];
+    } else {
+        uint32_t col[4][4];   // col[c][g]: variable jw + c, samples 16 sg + 4 g .. +3
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int rr = sg * 16 + g * 4;
+            const uint32_t w0 = nz_bytes(S32[(rr + 0) * (kTileJ / 4) + swz]);
+            const uint32_t w1 = nz_bytes(S32[(rr + 1) * (kTileJ / 4) + swz]);
+            const uint32_t w2 = nz_bytes(S32[(rr + 2) * (kTileJ / 4) + swz]);
+            const uint32_t w3 = nz_bytes(S32[(rr + 3) * (kTileJ / 4) + swz]);
+            acc4 += (w0 + w1) + (w2 + w3);
+            transpose4x4(w0, w1, w2, w3, col[0][g], col[1][g], col[2][g], col[3][g]);
         }
-        if (a.Bp != nullptr) {
-            const uint32_t bits = bytes_to_nibble(col[c][0]) |
-                                  (bytes_to_nibble(col[c][1]) << 4) |
-                                  (bytes_to_nibble(col[c][2]) << 8) |
-                                  (bytes_to_nibble(col[c][3]) << 12);
-            uint16_t* B16 = reinterpret_cast<uint16_t*>(a.Bp);
-            B16[j * (a.ldp / 16) + rbase / 16] = static_cast<uint16_t>(bits);
+        const int64_t rbase = tile * kTileR + sg * 16;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t j = jw + c;
+            if (j >= a.n) continue;   // padding rows are left as they are: masked downstream
+            if (a.P != nullptr) {
+                uint4 o;
+                o.x = col[c][0] * 0x38u;
+                o.y = col[c][1] * 0x38u;
+                o.z = col[c][2] * 0x38u;
+                o.w = col[c][3] * 0x38u;
+                *reinterpret_cast<uint4*>(a.P + (tile * a.rows_p + j) * kTileR + sg * 16) = o;
+            }
+            if (a.Bp != nullptr) {
+                const uint32_t bits = bytes_to_nibble(col[c][0]) |
+                                      (bytes_to_nibble(col[c][1]) << 4) |
+                                      (bytes_to_nibble(col[c][2]) << 8) |
+                                      (bytes_to_nibble(col[c][3]) << 12);
+                uint16_t* B16 = reinterpret_cast<uint16_t*>(a.Bp);
+                B16[j * (a.ldp / 16) + rbase / 16] = static_cast<uint16_t>(bits);
+            }
         }
     }
+    colsum[0] += acc4 & 0xFF;
+    colsum[1] += (acc4 >> 8) & 0xFF;
+    colsum[2] += (acc4 >> 16) & 0xFF;
+    colsum[3] += acc4 >> 24;
 }
 
 // Column sums of the CTA's variables: sum over the 8 sample groups of the warp
