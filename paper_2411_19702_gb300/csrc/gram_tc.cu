@@ -235,12 +235,15 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         const int brows = bn > kTcBM ? kTcBNMax : bn;
         const CUtensorMap* mapB = brows == 256 ? &maps.box256 : (brows == 128 ? &maps.box128
                                                                                : &maps.box64);
+        // pair: the partner CTA holds B rows [N/2, N) of the tile's MMA width N;
+        // each CTA's half is one box of 120 rows when N = 240, else of 128
+        const int nhalf = kPair ? tile_n(job, tile) / 2 : 0;
+        const bool half120 = kPair && nhalf == 120;
+        const CUtensorMap* mapH = half120 ? &maps.box120 : &maps.box128;
         const uint32_t bytes = static_cast<uint32_t>(
-            (Plan<kPair>::tile_m + (kPair ? 2 * kTcBM : brows)) * kTcBK);
+            (Plan<kPair>::tile_m + (kPair ? (half120 ? 240 : 2 * kTcBM) : brows)) * kTcBK);
         const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m;
         const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn;
-        // pair: the partner CTA holds B rows [N/2, N) of the tile's MMA width N
-        const int nhalf = kPair ? tile_n(job, tile) / 2 : 0;
         if (L.direct && ((a0 | b0) & 15) != 0) {
             // a direct copy's x coordinate (a variable index) must be a multiple
             // of 16 bytes: record it and issue nothing
@@ -263,11 +266,11 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
                 const int32_t ya = static_cast<int32_t>(a0 + k * job.strideA);
                 const int32_t yb = static_cast<int32_t>(b0 + k * job.strideB);
                 ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.box128, sm.full(stage), 0, ya);
-                ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), &maps.box128, sm.full(stage), 0, yb);
+                ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), mapH, sm.full(stage), 0, yb);
                 ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.a(stage)), 1u),
                                       &maps.box128, sm.full(stage), 0, ya + kTcBM);
                 ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.b(stage)), 1u),
-                                      &maps.box128, sm.full(stage), 0, yb + nhalf);
+                                      mapH, sm.full(stage), 0, yb + nhalf);
             } else if (L.direct) {
                 // 128 variables x 128 samples of X per box; B in bn / 128 boxes
                 const int32_t y = static_cast<int32_t>(k * kTcBK);
@@ -802,6 +805,7 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
             ptx::tma_prefetch_desc(&maps.xb);
         } else {
             ptx::tma_prefetch_desc(&maps.box64);
+            ptx::tma_prefetch_desc(&maps.box120);
             ptx::tma_prefetch_desc(&maps.box128);
             ptx::tma_prefetch_desc(&maps.box256);
         }

@@ -224,9 +224,10 @@ struct GramLaunch {
 };
 
 // TMA descriptors of a K-block-major operand buffer of total_rows rows of 128
-// bytes, for boxes of 64, 128 and 256 rows (128-byte swizzle).
+// bytes, for boxes of 64, 120, 128 and 256 rows (128-byte swizzle).
 struct OperandMaps {
     CUtensorMap box64, box128, box256;
+    CUtensorMap box120;   // a CTA's half of the B rows of a 240-wide FP4 pair tile
     // direct operands: X (A) and Y or X (B) themselves, row-major samples x
     // variables, boxes of 128 variables x 128 samples (128-byte swizzle)
     CUtensorMap xa, xb;

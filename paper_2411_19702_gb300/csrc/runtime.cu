@@ -355,6 +355,7 @@ bool make_direct_maps(OperandMaps* maps, const uint8_t* X, int64_t m, int64_t n1
 bool make_operand_maps(OperandMaps* maps, const uint8_t* P, int64_t total_rows) {
     if (total_rows <= 0 || total_rows >= (int64_t{1} << 31)) return false;
     return encode_box(&maps->box64, P, total_rows, 64) &&
+           encode_box(&maps->box120, P, total_rows, 120) &&
            encode_box(&maps->box128, P, total_rows, 128) &&
            encode_box(&maps->box256, P, total_rows, 256);
 }
