@@ -96,7 +96,8 @@ typedef enum {
                                     2 = whenever there are samples enough                        */
     GBMI_OPT_FP4 = 12            /* 1: the tensor-core paths (single calls, cross, host buffers,
                                     out-of-core, CSR densified, batches and servers created while
-                                    it is set; not mi_all_pairs_noalloc or GBMI_OPT_DIRECT)
+                                    it is set; mi_all_pairs_noalloc always uses FP4, and
+                                    GBMI_OPT_DIRECT reads X itself as FP8)
                                     pack X as FP4 (E2M1 0 / 1, two samples per byte) and run the
                                     block-scaled FP4 MMA (tcgen05 kind::mxf4, every scale factor
                                     1.0; tiles at most 240 wide): the same exact counts from half
@@ -158,9 +159,10 @@ gbmi_status mi_cross_host(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t
  *
  * X (m x n uint8 0/1) and out (n x n FP32) are caller-owned device pointers,
  * as for mi_all_pairs; the result is the fused tensor-core path's with the
- * FP32 epilogue (GBMI_OPT_FIXUP is ignored).  Limits: 1 <= m <= 2^24, and
- * n_pad(n) * m_pad(m) bytes of packed operand (n rounded up to 256, m to 128)
- * plus about 36 n bytes must fit in 64 MiB; larger problems return
+ * FP32 epilogue and FP4 operands (GBMI_OPT_FIXUP and GBMI_OPT_FP4 are
+ * ignored).  Limits: 1 <= m <= 2^24, and n_pad(n) * m_pad(m) / 2 bytes of
+ * packed operand (n rounded up to 256, m to 256) plus about 36 n bytes must
+ * fit in 64 MiB; larger problems return
  * GBMI_ERR_ARG with the required size in gbmi_last_error_string().
  *
  * The first call on each device looks up the array's device address (with

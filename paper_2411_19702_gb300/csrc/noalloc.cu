@@ -11,7 +11,7 @@
 // one never does.
 //
 // How: every buffer the fused tensor-core path needs besides the caller's
-// input and output (the packed FP8 operand, the column counts, the
+// input and output (the packed FP4 operand, the column counts, the
 // per-variable epilogue terms, the tile list and the device error word)
 // lives in one file-scope device array of kScratchBytes.  The array belongs
 // to this library's module, so every GPU that loads the module holds it until
@@ -39,7 +39,7 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t{64} << 20;   // 64 MiB
 constexpr int kMaxDev = 64;
-constexpr int kTileN = 256;                          // tile width used by this entry point
+constexpr int kTileN = kTcBNFp4;                     // tile width (FP4 operands: 240)
 constexpr int kGroupCols = 8;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
@@ -110,7 +110,7 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     if (n < 1 || n > (int64_t{1} << 20)) return na_fail(GBMI_ERR_ARG, "n out of range");
 
     // scratch layout: error word | v | per-variable terms | tile list | packed operand
-    const int64_t rows_p = pack_rows(n), kb = pack_ld(m) / kTcBK;
+    const int64_t rows_p = pack_rows(n), kb = pack_ld_of(m, true) / kKbSamplesFp4;
     const int TI = static_cast<int>((n + kTcBM - 1) / kTcBM);
     const int TJ = static_cast<int>((n + kTileN - 1) / kTileN);
     const int64_t ntiles = gram_tile_count(n, n, kTileN, true);
@@ -152,7 +152,8 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     pj.P = P;
     pj.v = v;
     pj.rows_p = rows_p;
-    pj.ldp = kb * kTcBK;
+    pj.ldp = kb * kKbSamplesFp4;
+    pj.fp4 = 1;
     if ((e = launch_pack(pj, s)) != cudaSuccess) return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
 
     MiParams mp;
@@ -194,6 +195,7 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     L.tiles = tiles;
     L.num_tiles = static_cast<int>(ntiles);
     L.mode = kTcModeMI;
+    L.fp4 = 1;
     L.err = err;
     L.timeout_ns = 2000000000ull;
     const int grid = static_cast<int>(std::min<int64_t>(g_na_sms[dev], ntiles));

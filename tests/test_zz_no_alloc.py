@@ -60,7 +60,7 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     lib = gbmi.load()
     X = torch.zeros((4, 4), dtype=torch.uint8, device="cuda")
     out = torch.empty((4, 4), dtype=torch.float32, device="cuda")
-    # 2^24 samples x 1000 variables needs about 16 GiB of packed operand
+    # 2^24 samples x 1000 variables needs about 8 GiB of packed FP4 operand
     st = lib.mi_all_pairs_noalloc(ctypes.c_void_p(X.data_ptr()), 1 << 24, 1000,
                                   ctypes.c_void_p(out.data_ptr()))
     assert st == gbmi.ERR_ARG
