@@ -1028,17 +1028,19 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
 }
 
 // Sparse input: which form is cheaper, by a model of GB300 rates measured on
-// this build (pair enumeration: about 5e10 atomic increments/s, plus the
+// this build (pair enumeration: about 4e10 atomic increments/s, plus the
 // elementwise MI; dense: zero + scatter + pack of m*n bytes at HBM rate, plus
-// the tensor-core Gram at about 3.8e15 flops/s).  The increments are
+// the tensor-core Gram at about 6.4e15 flops/s with FP4 operands, 3.8e15 with
+// FP8).  The increments are
 // estimated from nnz alone (equal row lengths: sum k(k+1)/2 >= nnz^2/(2m) +
 // nnz/2), so the call stays asynchronous; skewed rows only make the
 // enumeration look cheaper than it is.
 bool csr_dense_is_cheaper(int64_t m, int64_t n, int64_t nnz) {
     const double dm = static_cast<double>(m), dn = static_cast<double>(n);
     const double incr = static_cast<double>(nnz) * nnz / (2.0 * dm) + 0.5 * nnz;
-    const double t_enum = incr / 5.0e10 + dn * dn * 8.0 / 6.0e12;
-    const double t_dense = dm * dn * 3.0 / 6.0e12 + dm * dn * dn / 3.8e15;
+    const double t_enum = incr / 4.0e10 + dn * dn * 8.0 / 6.0e12;
+    const double gram_flops = g_opt.fp4 != 0 ? 6.4e15 : 3.8e15;
+    const double t_dense = dm * dn * 3.0 / 6.0e12 + dm * dn * dn / gram_flops;
     return t_dense < t_enum;
 }
 
