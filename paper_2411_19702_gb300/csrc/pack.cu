@@ -261,53 +261,47 @@ __device__ __forceinline__ void pack_cta_unaligned(const PackJob& a, const int64
     uint8_t* const wraw = raw + (t >> 5) * kRawWarpBytes;   // this warp's raw rows
     const int rr_w = (t >> 3) & 3;   // the lane's row among the warp's 4 per quarter
     const int gl = t & 7;            // and its granule
+    // The lane's rows are r = 32 k + t / 8; 32 ldx is a multiple of 16, so all
+    // of them start their slice at the same offset sft within a 16-byte
+    // granule, and the valid bytes of each granule are the same for all of them.
+    const int sft = static_cast<int>(
+        (reinterpret_cast<uintptr_t>(a.X + j0) + static_cast<uint64_t>(t >> 3) * a.ldx) & 15);
+    const int64_t keep_row = a.n - j0 < kTileJ ? a.n - j0 : kTileJ;   // >= 1
+    const int64_t end = sft + keep_row;   // valid bytes: [sft, end) of the row's granules
+    const uint32_t nb0 = static_cast<uint32_t>(
+        end - 16 * gl <= 0 ? 0 : (end - 16 * gl > 16 ? 16 : end - 16 * gl));
+    const uint32_t nb8 = static_cast<uint32_t>(end - 128 <= 0 ? 0 : end - 128);   // <= 16
+    // + r * ldx: the lane's granule of row r (the aligned granule holding the
+    // row's first byte, + 16 gl)
+    const uintptr_t G0 = reinterpret_cast<uintptr_t>(a.X + j0) - sft + 16 * gl;
     auto issue_tile = [&](int64_t tile) {
         const int64_t r0 = tile * kTileR;
-        const int64_t keep_row = a.n - j0 < kTileJ ? a.n - j0 : kTileJ;   // >= 1
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t r = r0 + q * 32 + (t >> 3);
             const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(
                 wraw + (4 * q + rr_w) * kRawRowBytes + 16 * gl));
-            if (r < a.m) {
-                const uintptr_t ad = reinterpret_cast<uintptr_t>(a.X + r * a.ldx + j0);
-                const int sft = static_cast<int>(ad & 15);
-                const uint8_t* G = reinterpret_cast<const uint8_t*>(ad - sft);
-                // valid bytes of granule k: [sft, sft + keep_row) in the row's granules
-                const int64_t end = sft + keep_row;
-                const int64_t n0 = end - 16 * gl;
-                cp_async16(dst, G + 16 * gl,
-                           static_cast<uint32_t>(n0 <= 0 ? 0 : (n0 > 16 ? 16 : n0)));
-                if (gl == 7) {
-                    const int64_t n8 = end - 128;
-                    cp_async16(dst + 16, G + 128,
-                               static_cast<uint32_t>(n8 <= 0 ? 0 : (n8 > 16 ? 16 : n8)));
-                }
-            } else {   // samples beyond m: zeros
-                cp_async16(dst, a.X, 0u);
-                if (gl == 7) cp_async16(dst + 16, a.X, 0u);
-            }
+            const bool in = r < a.m;   // samples beyond m: zeros
+            const uint8_t* G = reinterpret_cast<const uint8_t*>(G0 + r * a.ldx);
+            cp_async16(dst, in ? G : a.X, in ? nb0 : 0u);
+            if (gl == 7) cp_async16(dst + 16, in ? G + 16 : a.X, in ? nb8 : 0u);
         }
         cp_async_commit();
     };
     if (tile_begin < tile_end) issue_tile(tile_begin);
 
     int colsum[4] = {0, 0, 0, 0};
+    const uint32_t sh = static_cast<uint32_t>(sft & 3) * 8u;
     for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
-        const int64_t r0 = tile * kTileR;
         // this tile's raw rows have landed (the warp's own copies) -> realign
         cp_async_wait_all();
         __syncwarp();
-        const uint32_t* wr = reinterpret_cast<const uint32_t*>(wraw);
+        const uint32_t* wr =
+            reinterpret_cast<const uint32_t*>(wraw) + (sft >> 2) + 4 * gl + rr_w * (kRawRowBytes / 4);
         uint4 pre[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int64_t r = r0 + q * 32 + (t >> 3);
-            const int sft = r < a.m ? static_cast<int>(reinterpret_cast<uintptr_t>(
-                                                           a.X + r * a.ldx + j0) & 15)
-                                    : 0;
-            const uint32_t* row = wr + (4 * q + rr_w) * (kRawRowBytes / 4) + (sft >> 2) + 4 * gl;
-            const uint32_t sh = static_cast<uint32_t>(sft & 3) * 8u;
+            const uint32_t* row = wr + 4 * q * (kRawRowBytes / 4);
             const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3], w4 = row[4];
             pre[q] = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
                                 __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
