@@ -83,8 +83,9 @@ typedef enum {
                                     of device memory but measured slower (default 0)          */
     GBMI_OPT_PAIR = 9,           /* 1: the single-call and out-of-core tensor-core paths run the
                                     Gram on CTA pairs (clusters of two SMs sharing one tcgen05
-                                    cta_group::2 MMA of 256 x 256 x 32; each SM stages half of A
-                                    and half of B) whenever that keeps at least as many SMs busy as
+                                    cta_group::2 MMA tile of 256 x 240 with FP4 operands, 256 x 256
+                                    with FP8; each SM stages half of A and half of B) whenever
+                                    that keeps at least as many SMs busy as
                                     single-CTA tiles would; 2: always; 0: single-CTA tiles only
                                     (default 1)                                                  */
     GBMI_OPT_CSR_PATH = 10,      /* CSR input (gbmi_*_csr): 0 = by a cost model (default), 1 = pair
@@ -315,8 +316,9 @@ int64_t gbmi_batch_tiles(const gbmi_batch* plan);
  *
  * A request loop with continuous batching (no counterpart in the paper).
  * The server owns one device arena of budget_bytes from which it takes, per
- * dataset, the packed FP8 operand, the column counts and the per-variable
- * terms (resident until the dataset is removed), and per request its output.
+ * dataset, the packed operand (FP4 or FP8 as GBMI_OPT_FP4 was when the server
+ * was created), the column counts and the per-variable terms (resident until
+ * the dataset is removed), and per request its output.
  * A worker thread admits queued requests in arrival order whenever their
  * memory fits and fewer than max_batch requests are waiting for the GPU,
  * merges them into one grouped launch (pack of the datasets not yet resident,
