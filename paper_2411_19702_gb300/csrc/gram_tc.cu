@@ -230,8 +230,9 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         const GramTile tile = L.tiles[tid];
         const GramJob& job = job_of(L, tile.job);
         const int bn = job.bn;
-        // rows of B per stage: the tile width, 256 for a 240-wide FP4 tile (its
-        // MMAs read the first 240); a pair loads four 128-row boxes
+        // rows of B per stage on one CTA: the tile width, 256 for a 240-wide FP4
+        // tile (its MMAs read the first 240); a pair loads two 128-row boxes of A
+        // and two boxes of B (below)
         const int brows = bn > kTcBM ? kTcBNMax : bn;
         const CUtensorMap* mapB = brows == 256 ? &maps.box256 : (brows == 128 ? &maps.box128
                                                                                : &maps.box64);
