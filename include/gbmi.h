@@ -75,7 +75,8 @@ typedef enum {
     GBMI_OPT_GROUP_COLS = 4,     /* tile-order group width in 256-column blocks (default 8)      */
     GBMI_OPT_MAX_CTAS = 5,       /* cap on persistent CTAs, 0 = one per SM (default 0)           */
     GBMI_OPT_PROFILE = 6,        /* 1: time every kernel launch with CUDA events (default 0)     */
-    GBMI_OPT_TILE_N = 7,         /* tensor-core tile width 64/128/256; 0 = tuner / model (default) */
+    GBMI_OPT_TILE_N = 7,         /* tensor-core tile width 64/128/256 (256 runs 240 wide with FP4
+                                    operands); 0 = tuner / model (default)                        */
     GBMI_OPT_DIRECT = 8,         /* 1: tensor-core paths read X / Y directly, without the pack pass
                                     or its packed copy, when n (and n2) are multiples of 16 and X, Y
                                     are 16-byte aligned; bytes must then be 0 / 1 (others are
