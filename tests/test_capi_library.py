@@ -77,3 +77,16 @@ def test_host_call_fails_loudly_without_gpu(lib):
     X = np.zeros((8, 4), np.uint8)
     with pytest.raises(gbmi.GbmiError):
         gbmi.mi_all_pairs_host(X)
+
+
+def test_binding_option_numbers_match_the_header(lib):
+    """Every GBMI_OPT_* value of the header has the same number in the binding,
+    and every option, the operand form included, is accepted without a GPU."""
+    import re
+    text = open(gbmi.HEADER).read()
+    opts = dict((k, int(v)) for k, v in re.findall(r"GBMI_OPT_(\w+)\s*=\s*(\d+)", text))
+    assert "FP4" in opts and len(opts) >= 12
+    for name, value in opts.items():
+        assert getattr(gbmi, "OPT_" + name) == value, name
+    assert lib.gbmi_set_option(gbmi.OPT_FP4, 0) == gbmi.OK
+    assert lib.gbmi_set_option(gbmi.OPT_FP4, 1) == gbmi.OK
