@@ -33,6 +33,7 @@
 
 #include "gbmi.h"
 #include "internal.cuh"
+#include "runtime.h"
 
 namespace gbmi {
 namespace {
@@ -197,15 +198,18 @@ extern "C" gbmi_status mi_all_pairs_noalloc(const uint8_t* X, int64_t m, int64_t
     L.mode = kTcModeMI;
     L.fp4 = 1;
     L.err = err;
-    L.timeout_ns = 2000000000ull;
+    L.timeout_ns = rt::g_opt.timeout_ns;   // GBMI_OPT_TIMEOUT_NS, as for every other launch
     const int grid = static_cast<int>(std::min<int64_t>(g_na_sms[dev], ntiles));
     if ((e = launch_gram_tc(maps, L, grid, s)) != cudaSuccess)
         return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
 
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
+    // the error word comes back on the library stream: one wait for this
+    // call's own work, not for other streams of the device
     unsigned int host_err = 0;
-    if ((e = cudaMemcpy(&host_err, err, sizeof(host_err), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(&host_err, err, sizeof(host_err), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+        return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
         return na_fail(GBMI_ERR_CUDA, cudaGetErrorString(e));
     if (host_err != 0) return na_fail(GBMI_ERR_TIMEOUT, "a bounded device-side wait timed out");
     return GBMI_OK;

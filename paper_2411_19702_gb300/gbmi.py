@@ -199,6 +199,8 @@ def mi_all_pairs_noalloc(X, out):
     m, n = X.shape
     if out.shape != (n, n) or out.dtype != torch.float32 or not out.is_contiguous():
         raise ValueError("out must be a contiguous float32 (n, n) tensor")
+    if out.device != X.device:
+        raise ValueError("out must be on X's device")
     with torch.cuda.device(X.device):
         lib = _bind_stream(X.device)
         _check(lib.mi_all_pairs_noalloc(X.data_ptr(), m, n, out.data_ptr()))
