@@ -393,6 +393,22 @@ double gbmi_profile_ms(int k);
 int64_t gbmi_profile_launches(int k);
 gbmi_status gbmi_profile_reset(void);
 
+/* Tensor-core throughput of the Gram kernel's MMA forms, for its roofline
+ * (the paper has no counterpart; Sec. 3.2 puts the method's cost in the one
+ * Gram, so this is the rate that bounds it).  Every SM (every CTA pair when
+ * pair != 0) holds A and B tiles of random 0/1 values in shared memory and one
+ * thread issues `mmas` back-to-back tcgen05.mma of M x n x K into tensor
+ * memory: M = 128 (256 for a pair), K = 64 samples for fp4 != 0 (block-scaled
+ * E2M1, kind::mxf4, every scale factor 1.0) or 32 for FP8 E4M3
+ * (kind::f8f6f4), the instruction and shared-memory descriptors of the Gram
+ * kernel.  No global memory is read in the loop.  n: multiple of 16 in
+ * [16, 256]; mmas in [1, 2^32] (rounded up to a multiple of 16).  Synchronous
+ * on the library stream: *flops_per_s = 2 M n K x MMAs issued / elapsed time
+ * of the launch (CUDA events), *ms (may be null) = that time.  Errors:
+ * GBMI_ERR_ARG, GBMI_ERR_CUDA, GBMI_ERR_TIMEOUT (a bounded wait gave up). */
+gbmi_status gbmi_mma_peak(int fp4, int pair, int n, int64_t mmas, double* flops_per_s,
+                          double* ms);
+
 /* Library version, major*10000 + minor*100 + patch. */
 int gbmi_version(void);
 

@@ -41,6 +41,7 @@ struct DeviceCtx {
     bool ready = false;
     int sm_count = 0;
     DevBuf P, Ba, Bb, va, vb, ha, hb, counts, T, err, tiles, Xs, Ys, outs, flag;
+    DevBuf peak_err;   // error word of the tensor-core throughput probe
     DevBuf sched;   // tile counter of the Gram launches (zeroed before each launch)
     // split Gram (sample ranges as jobs): job table and tile list, host copies kept
     // alive for the asynchronous uploads

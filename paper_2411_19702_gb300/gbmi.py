@@ -76,6 +76,7 @@ def load(path: str | None = None):
             "gbmi_shutdown": [],
             "gbmi_profile_reset": [],
             "mi_all_pairs_noalloc": [vp, i64, i64, vp],
+            "gbmi_mma_peak": [i32, i32, i32, i64, vp, vp],
             "gbmi_tuner_set": [i64, i64, i32],
             "gbmi_tuner_clear": [],
             "gbmi_tile_n": [i64, i64],
@@ -558,6 +559,20 @@ def shutdown():
 
 def version() -> int:
     return int(load().gbmi_version())
+
+
+def mma_peak(fp4: bool = True, pair: bool = True, n: int = 256, mmas: int = 1 << 16) -> dict:
+    """Tensor-core throughput of one MMA form with shared-memory operands.
+
+    Marshals gbmi_mma_peak: every SM (or CTA pair) issues ``mmas`` MMAs of
+    M x n x K; returns ``{"flops_per_s": F, "ms": T}``.
+    """
+    import torch
+    f, t = ctypes.c_double(), ctypes.c_double()
+    lib = _bind_stream(torch.device("cuda", torch.cuda.current_device()))
+    _check(lib.gbmi_mma_peak(int(bool(fp4)), int(bool(pair)), int(n), int(mmas),
+                             ctypes.byref(f), ctypes.byref(t)))
+    return {"flops_per_s": f.value, "ms": t.value}
 
 
 def profile(enable: bool | None = None, reset: bool = False) -> dict:
