@@ -110,6 +110,66 @@ gbmi_status tile_list(DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn, 
     return GBMI_OK;
 }
 
+// Tail split of the fused MI launch: a persistent launch of T tiles on U
+// concurrent tile slots ends with a partial wave of T mod U tiles while the
+// other slots idle.  The last (T mod U) + U tiles are instead run as `parts`
+// units each accumulating 1 / parts of the samples, so the launch ends in
+// pieces half as long (GBMI_OPT_TAIL_SPLIT: 0 off, 1 on, k >= 2 every tile in
+// k parts).  Returns the number of split tiles (0: none).
+int tail_split_plan(int tiles, int units, int64_t k_blocks, int* parts) {
+    *parts = 0;
+    if (g_opt.tail_split == 0 || tiles <= 0 || units <= 0) return 0;
+    int S = 0, P = 2;
+    if (g_opt.tail_split >= 2) {
+        S = tiles;
+        P = g_opt.tail_split;
+    } else if (tiles >= units && tiles % units != 0) {
+        S = std::min(tiles, tiles % units + units);
+    }
+    if (S <= 0 || k_blocks < P) return 0;
+    *parts = P;
+    return S;
+}
+
+// The split tile list (the cached list c.tl_host with its last S tiles as
+// `parts` units each), uploaded to c.tail_tiles; part buffers sized.
+gbmi_status tail_split_list(DeviceCtx& c, int S, int parts, int* count) {
+    const int T = static_cast<int>(c.tl_host.size());
+    const int n = T - S + S * parts;
+    if (!(c.ts_key_tiles == T && c.ts_key_s == S && c.ts_key_p == parts &&
+          c.ts_key_na == c.tl_na && c.ts_key_nb == c.tl_nb && c.ts_key_bn == c.tl_bn &&
+          c.ts_key_bm == c.tl_bm && c.ts_key_group == c.tl_group)) {
+        c.ts_host.assign(c.tl_host.begin(), c.tl_host.begin() + (T - S));
+        for (int s = 0; s < S; ++s)
+            for (int p = 0; p < parts; ++p) {
+                GramTile g = c.tl_host[static_cast<size_t>(T - S + s)];
+                g.split = gram_split_code(s, p, parts);
+                c.ts_host.push_back(g);
+            }
+        GBMI_TRY(ensure(c.tail_tiles, c.ts_host.size() * sizeof(GramTile), "split tile list"));
+        GBMI_CUDA(cudaMemcpyAsync(c.tail_tiles.p, c.ts_host.data(),
+                                  c.ts_host.size() * sizeof(GramTile), cudaMemcpyHostToDevice,
+                                  g_stream),
+                  "split tile list upload");
+        c.ts_key_tiles = T;
+        c.ts_key_s = S;
+        c.ts_key_p = parts;
+        c.ts_key_na = c.tl_na;
+        c.ts_key_nb = c.tl_nb;
+        c.ts_key_bn = c.tl_bn;
+        c.ts_key_bm = c.tl_bm;
+        c.ts_key_group = c.tl_group;
+    }
+    GBMI_TRY(ensure(c.part_counts,
+                    static_cast<size_t>(S) * (parts - 1) * gram_part_slot_ints() * sizeof(int32_t),
+                    "split tile counts"));
+    GBMI_TRY(ensure(c.part_arrive,
+                    static_cast<size_t>(S) * gram_part_slot_counters() * sizeof(unsigned int),
+                    "split tile counters"));
+    *count = n;
+    return GBMI_OK;
+}
+
 // The CTA-pair kernel streams half the operand bytes per SM per MMA, so it is
 // taken whenever its launch keeps at least as many SMs busy as the single-CTA
 // launch of the same problem would (small problems keep the finer tiles).
@@ -313,6 +373,28 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     }
     const int grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, tiles))
                           : rt::grid_for(c, tiles);
+    // The MI launch (the last sample chunk) may split its last tiles into
+    // K-share units (tail_split): its own tile list, grid and part buffers.
+    const GramTile* const plain_tiles = L.tiles;
+    const int plain_num = L.num_tiles;
+    const GramTile* mi_tiles = plain_tiles;
+    int mi_num = plain_num, mi_grid = grid, split_slots = 0;
+    if (mode == kTcModeMI && !proto.mp.fixup && num_shards == 1 && dmaps == nullptr &&
+        proto.out_t == nullptr) {
+        const int64_t kb_last = kb_total - (kb_total - 1) / kb_chunk * kb_chunk;
+        const int units = pair ? static_cast<int>(std::min<int64_t>(c.pair_clusters, tiles))
+                               : grid;
+        int parts = 0;
+        split_slots = tail_split_plan(tiles, units, kb_last, &parts);
+        if (split_slots > 0) {
+            GBMI_TRY(tail_split_list(c, split_slots, parts, &mi_num));
+            mi_tiles = static_cast<const GramTile*>(c.tail_tiles.p);
+            mi_grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, mi_num))
+                           : rt::grid_for(c, mi_num);
+            L.part_counts = static_cast<int32_t*>(c.part_counts.p);
+            L.part_arrive = static_cast<unsigned int*>(c.part_arrive.p);
+        }
+    }
     for (int64_t k0 = 0; k0 < kb_total; k0 += kb_chunk) {
         L.job0.k_begin = static_cast<int32_t>(k0);
         L.job0.k_blocks = static_cast<int32_t>(std::min(kb_chunk, kb_total - k0));
@@ -324,8 +406,17 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
         } else {
             L.mode = k0 == 0 ? kTcModeCounts : kTcModeCountsAdd;
         }
+        const bool split = L.mode == kTcModeMI && split_slots > 0;
+        L.tiles = split ? mi_tiles : plain_tiles;
+        L.num_tiles = split ? mi_num : plain_num;
+        if (split)
+            GBMI_CUDA(cudaMemsetAsync(L.part_arrive, 0,
+                                      static_cast<size_t>(split_slots) *
+                                          gram_part_slot_counters() * sizeof(unsigned int),
+                                      g_stream),
+                      "split tile counters");
         GBMI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
-        GBMI_LAUNCH(launch_gram_tc(maps, L, grid, g_stream),
+        GBMI_LAUNCH(launch_gram_tc(maps, L, split ? mi_grid : grid, g_stream),
                     L.mode == kTcModeMI ? "gram_tc_fused_mi" : "gram_tc_counts");
     }
     return GBMI_OK;
@@ -1274,6 +1365,10 @@ gbmi_status gbmi_set_option(int option, int64_t value) {
         case GBMI_OPT_FP4:
             g_opt.fp4 = value != 0 ? 1 : 0;
             return GBMI_OK;
+        case GBMI_OPT_TAIL_SPLIT:
+            if (value < 0 || value > 15) return fail(GBMI_ERR_ARG, "tail split must be in [0, 15]");
+            g_opt.tail_split = static_cast<int>(value);
+            return GBMI_OK;
         case GBMI_OPT_CSR_PATH:
             if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "CSR path must be 0, 1 or 2");
             g_opt.csr_path = static_cast<int>(value);
@@ -1341,6 +1436,10 @@ gbmi_status gbmi_shutdown(void) {
         rt::release(c->split_jobs);
         rt::release(c->split_tiles);
         rt::release(c->split_part);
+        rt::release(c->tail_tiles);
+        rt::release(c->part_counts);
+        rt::release(c->part_arrive);
+        rt::release(c->peak_err);
         for (DevBuf* b : {&c->P, &c->Ba, &c->Bb, &c->va, &c->vb, &c->ha, &c->hb, &c->counts,
                           &c->T, &c->err, &c->tiles, &c->Xs, &c->Ys, &c->outs, &c->flag,
                           &c->panel})

@@ -18,8 +18,8 @@
 // bn (64, 128 or 256; at most 240 in an FP4 launch), its epilogue terms and its
 // output.
 //
-// Persistent, warp-specialised CTA, one per SM (576 threads; 320 for the
-// variant with the FP64 combine), or CTA pairs (clusters of 2, kPair):
+// Persistent, warp-specialised CTA, one per SM (576 threads), or CTA pairs
+// (clusters of 2, kPair):
 //   warp 0      TMA producer: per stage one 128 x 128-byte box of A (the
 //               variables of row block I) and one bn x 128-byte box of B
 //               (column block J) into a 4-stage shared-memory ring
@@ -35,11 +35,11 @@
 //               launches issue kind::mxf4.block_scale K=64 instead (N <= 240;
 //               the scale factors, all 1.0, sit in columns 240-255 and 496-511,
 //               filled by the epilogue warps before the first MMA).
-//   warps 2-17  epilogue (warps 2-9 for the FP64-combine variant), four (two)
-//               warps per TMEM lane quadrant (tcgen05.ld only reaches lanes
-//               32*(warp%4)..+31), each taking a quarter (half) of the tile's
-//               columns: load accumulator columns (one TMEM lane = one variable
-//               i per thread), derive n10, n01, n00, evaluate MI and store
+//   warps 2-17  epilogue, four warps per TMEM lane quadrant (tcgen05.ld only
+//               reaches lanes 32*(warp%4)..+31), each taking a quarter of the
+//               tile's columns: load accumulator columns (one TMEM lane = one
+//               variable i per thread), derive n10, n01, n00, evaluate MI (with
+//               the FP64 combine for small pairs when it is on) and store
 //               (i, j) as 16-, 8- or 4-byte pieces as the row's alignment
 //               allows and, for a symmetric problem, (j, i) as coalesced rows
 //               (or, for a panel of an out-of-core run, (j, i) into a separate
@@ -77,9 +77,35 @@ constexpr int kTcModeMI32 = 3;
 template <int kMode>
 __host__ __device__ constexpr bool is_mi() { return kMode == kTcModeMI || kMode == kTcModeMI32; }
 // Epilogue warps: 16 (four per TMEM lane quadrant) hide the latency of the
-// per-pair arithmetic; the FP64-combine variant needs too many registers for
-// 576 threads and keeps 8.
-__host__ __device__ constexpr int epi_warps(int mode) { return mode == kTcModeMI ? 8 : 16; }
+// per-pair arithmetic (and of the FP64 combine's table reads).  Epilogue warp
+// w (w = 2, 3, ...) serves TMEM lane
+// quadrant w % 4 (the only lanes its tcgen05.ld reaches), which is also the
+// SM sub-partition it is scheduled on; warp 0 (producer) and warp 1 (MMA
+// issuer) share sub-partitions 0 and 1 with the epilogue warps of quadrants 0
+// and 1.  Any count >= 4 works: a quadrant's warps split the tile's columns.
+constexpr int kEpiWarpsMain = 16;
+__host__ __device__ constexpr int epi_warps(int mode) { return kEpiWarpsMain; }
+// Epilogue warps serving the TMEM lane quadrant of warp w.
+__host__ __device__ constexpr int quadrant_warps(int nepi, int w) {
+    return (nepi - ((w - 2) & 3) + 3) / 4;
+}
+constexpr size_t kColVarTotal = 32768;   // staged column terms of all epilogue warps
+// Shared-memory bytes of one epilogue warp's column terms: an equal share,
+// rounded down to 32 bytes so that every warp's MiVar / MiVarF entries are
+// aligned for their vector stores and loads.
+__host__ __device__ constexpr size_t colvar_bytes(int nepi) {
+    return (kColVarTotal / nepi) & ~static_cast<size_t>(31);
+}
+// Most columns one epilogue warp takes of a 256-wide tile (its quadrant has at
+// least nepi / 4 warps; a warp's share is a multiple of 16).
+__host__ __device__ constexpr int max_part_cols(int nepi) {
+    return ((kTcBNMax + nepi / 4 - 1) / (nepi / 4) + 15) & ~15;
+}
+// int32 entries of one unit of a split tile (FP32 epilogue kernels): both CTAs
+// of a pair, every epilogue warp, its columns, 32 lanes.
+__host__ __device__ constexpr int64_t part_slot_ints() {
+    return int64_t{2} * kEpiWarpsMain * max_part_cols(kEpiWarpsMain) * 32;
+}
 __host__ __device__ constexpr int threads_of(int mode) { return 64 + 32 * epi_warps(mode); }
 constexpr int kUmmaK = 32;                       // bytes of K per MMA (32 FP8 or 64 FP4 samples)
 constexpr int kABytes = kTcBM * kTcBK;           // 16 KB: 128 rows of A
@@ -90,7 +116,6 @@ constexpr int kTmemCols = 2 * kAccCols;          // 512: the whole tensor memory
 constexpr int kSfaCol = kTcBNFp4;
 constexpr int kSfbCol = kAccCols + kTcBNFp4;
 constexpr uint32_t kScaleOnes = 0x7F7F7F7Fu;
-constexpr size_t kColVarTotal = 32768;           // staged column terms of all epilogue warps
 constexpr int kGroup = 16;                       // accumulator columns per tcgen05.ld
 constexpr int kQ = 8;                            // tile-id queue between the roles
 
@@ -123,9 +148,9 @@ struct Smem {
     uint32_t rank;   // CTA rank in the pair (0 when single)
     __device__ uint8_t* a(int s) const { return base + s * P::stage_bytes; }
     __device__ uint8_t* b(int s) const { return base + s * P::stage_bytes + kABytes; }
-    // column terms of epilogue warp e of nepi (kColVarTotal / nepi bytes each)
-    __device__ MiVar* colvars(int e, int nepi) const {
-        return reinterpret_cast<MiVar*>(base + P::off_colvars + e * (kColVarTotal / nepi));
+    // column terms of epilogue warp e of nepi (colvar_bytes(nepi) bytes each)
+    __device__ void* colvars(int e, int nepi) const {
+        return base + P::off_colvars + e * colvar_bytes(nepi);
     }
     __device__ uint64_t* bar(int k) const {
         return reinterpret_cast<uint64_t*>(base + P::off_bars) + k;
@@ -173,6 +198,20 @@ __device__ __forceinline__ int tile_n(const GramJob& job, const GramTile& tile) 
     if (w >= job.bn) return job.bn;
     const int n = static_cast<int>((w + 31) / 32 * 32);
     return n < 32 ? 32 : (n > job.bn ? job.bn : n);
+}
+
+// K blocks [kb0, kb1) of the job that a tile accumulates: all of them, or its
+// part's share for a split tile.
+__device__ __forceinline__ void tile_krange(const GramJob& job, const GramTile& tile, int& kb0,
+                                            int& kb1) {
+    if (tile.split == 0) {
+        kb0 = 0;
+        kb1 = job.k_blocks;
+        return;
+    }
+    const int parts = tile.split & 15, part = (tile.split >> 4) & 15;
+    kb0 = static_cast<int>(static_cast<int64_t>(job.k_blocks) * part / parts);
+    kb1 = static_cast<int>(static_cast<int64_t>(job.k_blocks) * (part + 1) / parts);
 }
 
 // ------------------------------------------------------------------ producer
@@ -252,7 +291,9 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
             ok = false;
             break;
         }
-        for (int kb = 0; kb < job.k_blocks; ++kb) {
+        int kb_lo = 0, kb_hi = 0;
+        tile_krange(job, tile, kb_lo, kb_hi);
+        for (int kb = kb_lo; kb < kb_hi; ++kb) {
             if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, L.timeout_ns,
                                         sm.abort_flag())) {
                 raise_abort(sm, L.err, kErrTimeoutLoad);
@@ -345,7 +386,9 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
             : L.direct ? ptx::idesc_e4m3_f32_mnmajor(kTcBM, static_cast<uint32_t>(job.bn))
                        : ptx::idesc_e4m3_f32(kTcBM, mma_n);
         const uint32_t sfa = tmem_base + kSfaCol, sfb = tmem_base + kSfbCol;
-        const int k_blocks = job.k_blocks;
+        int kb_lo = 0, kb_hi = 0;
+        tile_krange(job, tile, kb_lo, kb_hi);
+        const int k_blocks = kb_hi - kb_lo;
         if (!ptx::mbar_wait_bounded(sm.tempty(acc), acc_phase ^ 1u, L.timeout_ns,
                                     sm.abort_flag())) {
             raise_abort(sm, L.err, kErrTimeoutMma);
@@ -463,9 +506,17 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
     const int lane = threadIdx.x & 31;
     const int lane_base = (warp & 3) * 32;             // TMEM lanes this warp may access
     constexpr int kNepi = epi_warps(kMode);
-    constexpr int kParts = kNepi / 4;                  // warps per TMEM lane quadrant
+    const int nparts = quadrant_warps(kNepi, warp);    // warps of this TMEM lane quadrant
     const int part = (warp - 2) >> 2;                  // which part of the tile's columns
-    MiVar* cv = sm.colvars(warp - 2, kNepi);           // this warp's column terms
+    // this warp's column terms: the whole MiVar with the FP64 combine, else
+    // its 16-byte FP32 part
+    MiVar* cv = static_cast<MiVar*>(sm.colvars(warp - 2, kNepi));
+    MiVarF* cvf = static_cast<MiVarF*>(sm.colvars(warp - 2, kNepi));
+    static_assert(!is_mi<kMode>() ||
+                      colvar_bytes(kNepi) >=
+                          max_part_cols(kNepi) *
+                              (kMode == kTcModeMI32 ? sizeof(MiVarF) : sizeof(MiVar)),
+                  "column-term staging does not fit");
     const float cscale = L.direct ? 262144.f : 1.f;    // 2^18: direct operands hold 2^-9
     constexpr bool kFix = kMode == kTcModeMI;          // FP64 combine compiled in
     int acc = 0;
@@ -498,7 +549,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
         // job table and force these fields to be reloaded after every store
         const MiParams P = job.mp;
         // columns of this warp: a multiple of 16 (240-wide tiles: 64, 64, 64, 48)
-        const int per = ((job.bn / kParts) + 15) & ~15;
+        const int per = ((job.bn + nparts - 1) / nparts + 15) & ~15;
         const int col_base = part * per;
         const int cols = max(0, min(per, job.bn - col_base));
         const int64_t n_a = job.n_a, n_b = job.n_b;
@@ -519,7 +570,9 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             __syncwarp();
             for (int k = lane; k < cols; k += 32) {
                 const int64_t j = jstart + k;
-                if (j < n_b) {
+                if (kMode == kTcModeMI32) {
+                    cvf[k] = j < n_b ? load_var_f(job.vb + j) : MiVarF{0, 0.f, 0.f, 0.f};
+                } else if (j < n_b) {
                     cv[k] = load_var(job.vb + j);
                 } else {
                     cv[k] = A;
@@ -535,11 +588,15 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
         ptx::tc_fence_after();
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(lane_base) << 16) +
                                static_cast<uint32_t>(acc * kAccCols + col_base);
-        if constexpr (kMode == kTcModeMI32) {
-            // FP32 MI: chunks of 4 columns in one small loop body; the next
-            // chunk's accumulator columns load from TMEM during this chunk's math
+        if constexpr (is_mi<kMode>()) {
+            // MI: chunks of 4 columns in one small loop body; the next chunk's
+            // accumulator columns load from TMEM during this chunk's math.
+            // With the FP64 combine compiled in (kFix), pairs whose FP32 value
+            // is below the threshold (or surely below it by the chi-square
+            // bound) are recomputed in FP64 from the n log2 n table, the four
+            // pairs' table reads of a chunk issued together.
             const int64_t c_end64 = n_b - jstart < cols ? n_b - jstart : cols;
-            const int c_end = c_end64 <= 0 ? 0 : static_cast<int>((c_end64 + 3) & ~int64_t{3});
+            int c_end = c_end64 <= 0 ? 0 : static_cast<int>((c_end64 + 3) & ~int64_t{3});
             int c = 0;
             if (sym && ibase > jstart)   // chunks entirely below the diagonal for all 32 rows
                 c = static_cast<int>(((ibase - jstart) / 4) * 4);
@@ -548,6 +605,75 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             const int64_t ld_out = job.ld_out, ld_t = job.ld_t;
             // counts of earlier sample chunks (or null): n11 = prefix + this launch's
             const int32_t* const prefix = job.out_c;
+            // split tile: units 0 .. parts-2 store their exact counts in their
+            // slots and count themselves in; the last unit (listed, so taken,
+            // after the others) waits for them, adds their counts to its
+            // accumulator in tensor memory (exact: a launch counts at most
+            // 2^24 samples) and evaluates MI as for a whole tile.  The wait
+            // ends: the units it waits for are earlier in the tile list, so
+            // none of them waits on it.
+            if (tile.split != 0) {
+                const int parts = tile.split & 15, part = (tile.split >> 4) & 15;
+                const int64_t slot = (tile.split >> 8) - 1;
+                const int64_t wbase = (static_cast<int64_t>(sm.rank) * kNepi + (warp - 2)) *
+                                      max_part_cols(kNepi) * 32;
+                int32_t* const slot_base = L.part_counts + slot * (parts - 1) * part_slot_ints();
+                unsigned int* const arrive =
+                    L.part_arrive + (slot * 2 + sm.rank) * kNepi + (warp - 2);
+                if (part < parts - 1) {
+                    int32_t* mine = slot_base + part * part_slot_ints() + wbase;
+#pragma unroll 1
+                    for (int cc = c; cc < c_end; cc += 4) {
+                        uint32_t r4[4];
+                        ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(cc), r4);
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            mine[(cc + q) * 32 + lane] =
+                                __float2int_rn(__uint_as_float(r4[q]) * cscale);
+                    }
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) atomicAdd(arrive, 1u);
+                    c_end = c;   // the last unit evaluates this tile
+                } else {
+                    bool ready = true;
+                    if (lane == 0) {
+                        const uint64_t t0 = ptx::globaltimer_ns();
+                        while (*reinterpret_cast<volatile unsigned int*>(arrive) + 1u <
+                               static_cast<unsigned int>(parts)) {
+                            if (*sm.abort_flag() || ptx::globaltimer_ns() - t0 > L.timeout_ns) {
+                                ready = false;
+                                break;
+                            }
+                        }
+                    }
+                    ready = __shfl_sync(0xffffffffu, ready ? 1 : 0, 0) != 0;
+                    if (!ready) {
+                        if (lane == 0) raise_abort(sm, L.err, kErrTimeoutEpilogue);
+                        c_end = c;
+                    } else {
+                        __threadfence();   // the other units' counts are visible past this point
+                        const int32_t* others = slot_base + wbase;
+#pragma unroll 1
+                        for (int cc = c; cc < c_end; cc += 4) {
+                            uint32_t r4[4];
+                            ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(cc), r4);
+                            ptx::tmem_wait_ld();
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                float f = __uint_as_float(r4[q]);
+                                for (int pp = 0; pp < parts - 1; ++pp)
+                                    f += static_cast<float>(__ldcg(
+                                        others + pp * part_slot_ints() + (cc + q) * 32 + lane));
+                                r4[q] = __float_as_uint(f);
+                            }
+                            ptx::tmem_st_32x32b_x4(taddr + static_cast<uint32_t>(cc), r4);
+                        }
+                        ptx::tmem_wait_st();
+                    }
+                }
+            }
             uint32_t cur[4];
             if (c < c_end) {
                 ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(c), cur);
@@ -560,6 +686,8 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                 if (more) ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(c + 4), nxt);
                 const int64_t j0 = jstart + c;
                 float v[4];
+                int32_t n11s[4];
+                uint32_t need = 0;   // kFix: pairs that go to the FP64 combine
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int64_t j = j0 + q;
@@ -567,12 +695,52 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                     float mi = 0.f;
                     if (row_ok && j < n_b && (!sym || j >= i)) {
                         if (prefix != nullptr) n11 += prefix[i * ld_out + j];
-                        const MiVar B = cv[c + q];
-                        const MiCounts cc = mi_counts(n11, A.v, B.v, P);
-                        if (cc.det != 0)
-                            mi = fmaxf(mi_fp32(cc, static_cast<float>(cc.det), A, B, P), 0.f);
+                        if constexpr (kFix) {
+                            const MiVar B = cv[c + q];
+                            const MiCounts cc = mi_counts(n11, A.v, B.v, P);
+                            if (cc.det != 0) {
+                                const float fdet = static_cast<float>(cc.det);
+                                bool small = P.fixup && mi_surely_small(fdet, A, B, P);
+                                if (!small) {
+                                    mi = fmaxf(mi_fp32(cc, fdet, A, B, P), 0.f);
+                                    small = P.fixup && mi < P.fixup_below;
+                                }
+                                if (small) need |= 1u << q;
+                            }
+                        } else {
+                            const MiVarF B = cvf[c + q];
+                            const MiCounts cc = mi_counts(n11, A.v, B.v, P);
+                            if (cc.det != 0)
+                                mi = fmaxf(mi_fp32(cc, static_cast<float>(cc.det), A, B, P), 0.f);
+                        }
                     }
                     v[q] = mi;
+                    n11s[q] = n11;
+                }
+                if constexpr (kFix) {
+                    if (__any_sync(0xffffffffu, need != 0)) {
+                        // m MI = T[n11] + T[n10] + T[n01] + T[n00] - H_i - H_j + T[m]
+                        double t[4][4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const bool on = (need >> q) & 1u;
+                            const MiCounts cc = mi_counts(on ? n11s[q] : 0, on ? A.v : 0,
+                                                          on ? cv[c + q].v : 0, P);
+                            t[q][0] = on ? nlog2n(cc.n11, P) : 0.0;
+                            t[q][1] = on ? nlog2n(cc.n00, P) : 0.0;
+                            t[q][2] = on ? nlog2n(cc.n10, P) : 0.0;
+                            t[q][3] = on ? nlog2n(cc.n01, P) : 0.0;
+                        }
+                        const double Tm = nlog2n(P.m, P);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if ((need >> q) & 1u) {
+                                const double sum = (t[q][0] + t[q][1]) + (t[q][2] + t[q][3]);
+                                const double r = sum + (Tm - (A.h + cv[c + q].h));
+                                v[q] = fmaxf(static_cast<float>(r) * P.inv_m, 0.f);
+                            }
+                        }
+                    }
                 }
                 if (row_ok) {
 #pragma unroll
@@ -618,68 +786,10 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             uint32_t r[kGroup];
             ptx::tmem_ld_32x32b_x16(taddr + static_cast<uint32_t>(g), r);
             ptx::tmem_wait_ld();
-            if (is_mi<kMode>()) {
-                // pass 1: FP32 MI, or a mark for the FP64 combine
-                uint32_t need64 = 0;
+            // counts: the accumulator's exact integers
 #pragma unroll
-                for (int q = 0; q < kGroup; ++q) {
-                    const int64_t j = j0 + q;
-                    int32_t n11 = __float2int_rn(__uint_as_float(r[q]) * cscale);
-                    float mi = 0.f;
-                    if (row_ok && j < n_b && (!sym || j >= i)) {
-                        // counts of earlier sample chunks (or null)
-                        if (job.out_c != nullptr) n11 += job.out_c[i * job.ld_out + j];
-                        const MiVar B = cv[g + q];
-                        const MiCounts c = mi_counts(n11, A.v, B.v, P);
-                        if (c.det != 0) {
-                            const float fdet = static_cast<float>(c.det);
-                            bool small = kFix && P.fixup && mi_surely_small(fdet, A, B, P);
-                            if (!small) {
-                                mi = fmaxf(mi_fp32(c, fdet, A, B, P), 0.f);
-                                small = kFix && P.fixup && mi < P.fixup_below;
-                            }
-                            if (small) need64 |= 1u << q;
-                        }
-                    }
-                    r[q] = need64 & (1u << q) ? static_cast<uint32_t>(n11)
-                                              : __float_as_uint(mi);
-                }
-                // pass 2: FP64 n log n combine, table reads issued four pairs at a time
-                if (kFix && __any_sync(0xffffffffu, need64 != 0)) {
-#pragma unroll
-                    for (int q0 = 0; q0 < kGroup; q0 += 4) {
-                        double tv[4][4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int q = q0 + u;
-                            const bool on = (need64 >> q) & 1u;
-                            const int32_t n11 = on ? static_cast<int32_t>(r[q]) : 0;
-                            const int32_t vj = on ? cv[g + q].v : 0;
-                            const MiCounts c = on ? mi_counts(n11, A.v, vj, P)
-                                                  : MiCounts{0, 0, 0, 0, 0};
-                            tv[u][0] = nlog2n(c.n11, P);
-                            tv[u][1] = nlog2n(c.n00, P);
-                            tv[u][2] = nlog2n(c.n10, P);
-                            tv[u][3] = nlog2n(c.n01, P);
-                        }
-                        const double Tm = nlog2n(P.m, P);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int q = q0 + u;
-                            if ((need64 >> q) & 1u) {
-                                const double s = (tv[u][0] + tv[u][1]) + (tv[u][2] + tv[u][3]);
-                                const double rr = s + (Tm - (A.h + cv[g + q].h));
-                                r[q] = __float_as_uint(
-                                    fmaxf(static_cast<float>(rr) * P.inv_m, 0.f));
-                            }
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < kGroup; ++q)
-                    r[q] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[q]) * cscale));
-            }
+            for (int q = 0; q < kGroup; ++q)
+                r[q] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[q]) * cscale));
             // (j, i): lanes hold consecutive i -> each store is one coalesced row segment
             if (sym && row_ok) {
 #pragma unroll
@@ -688,30 +798,12 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                     if (j < n_b && j > i) store_one<kMode>(job, j, i, r[q]);
                 }
             }
-            // mirror into a separate buffer (panels of an out-of-core run)
-            if (is_mi<kMode>() && job.out_t != nullptr && row_ok) {
-#pragma unroll
-                for (int q = 0; q < kGroup; ++q) {
-                    const int64_t j = j0 + q;
-                    if (j < n_b) job.out_t[j * job.ld_t + i] = __uint_as_float(r[q]);
-                }
-            }
             // (i, j): 16 consecutive columns of this thread's row
             if (!row_ok) continue;
             const bool full = (j0 + kGroup <= n_b) && (!sym || j0 >= i);
-            const uintptr_t rowp = is_mi<kMode>()
-                                       ? reinterpret_cast<uintptr_t>(job.out_f + i * job.ld_out + j0)
-                                       : reinterpret_cast<uintptr_t>(job.out_c + i * job.ld_out + j0);
+            const uintptr_t rowp = reinterpret_cast<uintptr_t>(job.out_c + i * job.ld_out + j0);
             if (full && (rowp & 15u) == 0) {
-                if (is_mi<kMode>()) {
-                    float4* dst = reinterpret_cast<float4*>(job.out_f + i * job.ld_out + j0);
-#pragma unroll
-                    for (int q = 0; q < kGroup / 4; ++q)
-                        dst[q] = make_float4(__uint_as_float(r[4 * q]),
-                                             __uint_as_float(r[4 * q + 1]),
-                                             __uint_as_float(r[4 * q + 2]),
-                                             __uint_as_float(r[4 * q + 3]));
-                } else {
+                {
                     int4* dst = reinterpret_cast<int4*>(job.out_c + i * job.ld_out + j0);
 #pragma unroll
                     for (int q = 0; q < kGroup / 4; ++q) {
@@ -920,6 +1012,9 @@ int gram_tc_epilogue_warps(int mode, int fixup) {
     const int m = (mode == kTcModeMI && !fixup) ? kTcModeMI32 : mode;
     return epi_warps(m);
 }
+
+int64_t gram_part_slot_ints() { return part_slot_ints(); }
+int gram_part_slot_counters() { return 2 * kEpiWarpsMain; }
 
 int gram_tc_pair_clusters() {
     cudaLaunchConfig_t cfg;

@@ -176,9 +176,20 @@ struct GramJob {
 };
 
 // One 128 x bn output tile: job index, row block I, column block J.
+// split = 0: the whole tile.  Otherwise the tile is one of `parts` units that
+// each accumulate a contiguous share of the job's K blocks:
+//   split = ((slot + 1) << 8) | (part << 4) | parts   (2 <= parts <= 15)
+// Units 0 .. parts-2 store their exact int32 counts in the slot's part of
+// GramLaunch.part_counts and count themselves in on the slot's counters; unit
+// parts-1, listed after them, waits for them, adds their counts to its own and
+// runs the MI epilogue (the tail of a launch finishes in pieces of 1 / parts
+// of a tile, so fewer SMs idle).
 struct GramTile {
-    int32_t job, I, J, pad;
+    int32_t job, I, J, split;
 };
+__host__ __device__ inline int32_t gram_split_code(int slot, int part, int parts) {
+    return ((slot + 1) << 8) | (part << 4) | parts;
+}
 
 struct GramLaunch {
     const GramJob* jobs;       // device table, or null: every tile uses job0
@@ -221,7 +232,18 @@ struct GramLaunch {
     // scale factor 1.0): 0 and 1 are exact in E2M1, so the counts are the
     // same integers.  Packed operands only; every job has bn <= 240.
     int fp4;
+    // Split tiles (GramTile.split != 0; FP32 MI epilogue only): per slot the
+    // int32 counts of its first parts-1 units (gram_part_slot_ints() ints per
+    // unit, laid out per CTA rank, epilogue warp, column and lane), and one
+    // arrival counter per slot, CTA rank and epilogue warp (zero at launch).
+    int32_t* part_counts;
+    unsigned int* part_arrive;
 };
+// int32 entries of one part of a split tile in GramLaunch.part_counts (both
+// CTAs of a pair, every epilogue warp, its columns, 32 lanes).
+int64_t gram_part_slot_ints();
+// Arrival counters of one split slot.
+int gram_part_slot_counters();
 
 // TMA descriptors of a K-block-major operand buffer of total_rows rows of 128
 // bytes, for boxes of 64, 120, 128 and 256 rows (128-byte swizzle).

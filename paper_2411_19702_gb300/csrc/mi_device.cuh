@@ -60,6 +60,17 @@ struct __align__(16) MiVar {
     double unused;
 };
 
+// The FP32 terms of a MiVar (its first 16 bytes): all the FP32 epilogue reads.
+struct __align__(16) MiVarF {
+    int32_t v;
+    float r1, r0, rchi;
+};
+
+__device__ __forceinline__ MiVarF load_var_f(const MiVar* p) {
+    const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+    return MiVarF{__float_as_int(f.x), f.y, f.z, f.w};
+}
+
 __device__ __forceinline__ MiVar load_var(const MiVar* p) {
     MiVar r;
     const float4 f = __ldg(reinterpret_cast<const float4*>(p));
@@ -143,9 +154,10 @@ __device__ __forceinline__ bool mi_surely_small(float fdet, const MiVar& A, cons
     return (fdet * fdet) * (A.rchi * B.rchi) < P.chi_below;
 }
 
-// FP32 MI in bits (det != 0).
-__device__ __forceinline__ float mi_fp32(const MiCounts& c, float fdet, const MiVar& A,
-                                         const MiVar& B, const MiParams& P) {
+// FP32 MI in bits (det != 0); A and B are MiVar or MiVarF.
+template <class VA, class VB>
+__device__ __forceinline__ float mi_fp32(const MiCounts& c, float fdet, const VA& A,
+                                         const VB& B, const MiParams& P) {
     const float sdm = fdet * P.inv_m;
     const float r11 = A.r1 * B.r1, r10 = A.r1 * B.r0, r01 = A.r0 * B.r1, r00 = A.r0 * B.r0;
     const float t11 = mi_cell(c.n11, fdet * r11, sdm, r11, P);

@@ -31,7 +31,8 @@ bool log_errors() {
 }
 
 // Option defaults from the environment (GBMI_FIXUP, GBMI_TILE_N, GBMI_PAIR,
-// GBMI_DIRECT, GBMI_FP4, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS), read once
+// GBMI_DIRECT, GBMI_FP4, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS,
+// GBMI_TAIL_SPLIT), read once
 // when the library loads; values out of range are ignored.
 struct EnvOptions {
     EnvOptions() {
@@ -58,6 +59,7 @@ struct EnvOptions {
             g_opt.timeout_ns = static_cast<uint64_t>(v);
         if (num("GBMI_GROUP_COLS", 1, 1 << 20, &v)) g_opt.group_cols = static_cast<int>(v);
         if (num("GBMI_MAX_CTAS", 0, 1 << 20, &v)) g_opt.max_ctas = static_cast<int>(v);
+        if (num("GBMI_TAIL_SPLIT", 0, 15, &v)) g_opt.tail_split = static_cast<int>(v);
     }
 };
 EnvOptions g_env_options;

@@ -35,6 +35,7 @@ struct Options {
     int csr_path = 0;                    // CSR input: 0 cost model, 1 pair enumeration, 2 dense
     int split_k = 0;                     // sample split of few-tile Grams: 0 auto, 1 off, 2 forced
     int fp4 = 1;                         // tensor-core operands in the FP4 form (block-scaled MMA)
+    int tail_split = 0;                  // fused MI launch: last tiles in K-share units (off)
 };
 
 struct DeviceCtx {
@@ -62,6 +63,13 @@ struct DeviceCtx {
     unsigned int* dflags = nullptr;   // its device address
     int hflags_cap = 0;
     std::vector<GramTile> tl_host;
+    // split tile list of the fused MI launch (the cached list with its last
+    // tiles as K-share units), keyed by the cached list and the split
+    DevBuf tail_tiles, part_counts, part_arrive;
+    std::vector<GramTile> ts_host;
+    int ts_key_tiles = -1, ts_key_s = -1, ts_key_p = -1, ts_key_bn = -1, ts_key_bm = -1,
+        ts_key_group = -1;
+    int64_t ts_key_na = -1, ts_key_nb = -1;
 };
 
 extern std::recursive_mutex g_mu;
