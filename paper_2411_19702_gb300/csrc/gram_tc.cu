@@ -18,7 +18,7 @@
 // bn (64, 128 or 256; at most 240 in an FP4 launch), its epilogue terms and its
 // output.
 //
-// Persistent, warp-specialised CTA, one per SM (576 threads), or CTA pairs
+// Persistent, warp-specialised CTA, one per SM (448 threads), or CTA pairs
 // (clusters of 2, kPair):
 //   warp 0      TMA producer: per stage one 128 x 128-byte box of A (the
 //               variables of row block I) and one bn x 128-byte box of B
@@ -35,9 +35,9 @@
 //               launches issue kind::mxf4.block_scale K=64 instead (N <= 240;
 //               the scale factors, all 1.0, sit in columns 240-255 and 496-511,
 //               filled by the epilogue warps before the first MMA).
-//   warps 2-17  epilogue, four warps per TMEM lane quadrant (tcgen05.ld only
-//               reaches lanes 32*(warp%4)..+31), each taking a quarter of the
-//               tile's columns: load accumulator columns (one TMEM lane = one
+//   warps 2-13  epilogue, three warps per TMEM lane quadrant (tcgen05.ld
+//               only reaches lanes 32*(warp%4)..+31), each taking a third of
+//               the tile's columns: load accumulator columns (one TMEM lane = one
 //               variable i per thread), derive n10, n01, n00, evaluate MI (with
 //               the FP64 combine for small pairs when it is on) and store
 //               (i, j) as 16-, 8- or 4-byte pieces as the row's alignment
@@ -76,14 +76,17 @@ namespace {
 constexpr int kTcModeMI32 = 3;
 template <int kMode>
 __host__ __device__ constexpr bool is_mi() { return kMode == kTcModeMI || kMode == kTcModeMI32; }
-// Epilogue warps: 16 (four per TMEM lane quadrant) hide the latency of the
-// per-pair arithmetic (and of the FP64 combine's table reads).  Epilogue warp
+// Epilogue warps: 12 (three per TMEM lane quadrant) hide the latency of the
+// per-pair arithmetic and of the FP64 combine's table reads; more of them
+// delay the producer and MMA threads, which share sub-partitions 0 and 1 with
+// them (measured at 10^5 x 10^4: 16 warps 1.791 / 3.089 ms per call without /
+// with the FP64 combine, 12 warps 1.785 / 2.769 ms).  Epilogue warp
 // w (w = 2, 3, ...) serves TMEM lane
 // quadrant w % 4 (the only lanes its tcgen05.ld reaches), which is also the
 // SM sub-partition it is scheduled on; warp 0 (producer) and warp 1 (MMA
 // issuer) share sub-partitions 0 and 1 with the epilogue warps of quadrants 0
 // and 1.  Any count >= 4 works: a quadrant's warps split the tile's columns.
-constexpr int kEpiWarpsMain = 16;
+constexpr int kEpiWarpsMain = 12;
 __host__ __device__ constexpr int epi_warps(int mode) { return kEpiWarpsMain; }
 // Epilogue warps serving the TMEM lane quadrant of warp w.
 __host__ __device__ constexpr int quadrant_warps(int nepi, int w) {
@@ -508,14 +511,14 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
     constexpr int kNepi = epi_warps(kMode);
     const int nparts = quadrant_warps(kNepi, warp);    // warps of this TMEM lane quadrant
     const int part = (warp - 2) >> 2;                  // which part of the tile's columns
-    // this warp's column terms: the whole MiVar with the FP64 combine, else
-    // its 16-byte FP32 part
-    MiVar* cv = static_cast<MiVar*>(sm.colvars(warp - 2, kNepi));
+    // this warp's column terms: the 16-byte FP32 part of each MiVar and, with
+    // the FP64 combine, its FP64 entropy term in a second array
     MiVarF* cvf = static_cast<MiVarF*>(sm.colvars(warp - 2, kNepi));
+    double* cvh = reinterpret_cast<double*>(cvf + max_part_cols(kNepi));
     static_assert(!is_mi<kMode>() ||
                       colvar_bytes(kNepi) >=
                           max_part_cols(kNepi) *
-                              (kMode == kTcModeMI32 ? sizeof(MiVarF) : sizeof(MiVar)),
+                              (sizeof(MiVarF) + (kMode == kTcModeMI ? sizeof(double) : 0)),
                   "column-term staging does not fit");
     const float cscale = L.direct ? 262144.f : 1.f;    // 2^18: direct operands hold 2^-9
     constexpr bool kFix = kMode == kTcModeMI;          // FP64 combine compiled in
@@ -570,13 +573,8 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             __syncwarp();
             for (int k = lane; k < cols; k += 32) {
                 const int64_t j = jstart + k;
-                if (kMode == kTcModeMI32) {
-                    cvf[k] = j < n_b ? load_var_f(job.vb + j) : MiVarF{0, 0.f, 0.f, 0.f};
-                } else if (j < n_b) {
-                    cv[k] = load_var(job.vb + j);
-                } else {
-                    cv[k] = A;
-                }
+                cvf[k] = j < n_b ? load_var_f(job.vb + j) : MiVarF{0, 0.f, 0.f, 0.f};
+                if (kFix) cvh[k] = j < n_b ? __ldg(&job.vb[j].h) : 0.0;
             }
             if (row_ok) A = load_var(job.va + i);
             __syncwarp();
@@ -696,7 +694,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                     if (row_ok && j < n_b && (!sym || j >= i)) {
                         if (prefix != nullptr) n11 += prefix[i * ld_out + j];
                         if constexpr (kFix) {
-                            const MiVar B = cv[c + q];
+                            const MiVarF B = cvf[c + q];
                             const MiCounts cc = mi_counts(n11, A.v, B.v, P);
                             if (cc.det != 0) {
                                 const float fdet = static_cast<float>(cc.det);
@@ -719,24 +717,23 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                 }
                 if constexpr (kFix) {
                     if (__any_sync(0xffffffffu, need != 0)) {
-                        // m MI = T[n11] + T[n10] + T[n01] + T[n00] - H_i - H_j + T[m]
+                        // m MI = T[n11] + T[n10] + T[n01] + T[n00] + K_i + K_j
                         double t[4][4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const bool on = (need >> q) & 1u;
                             const MiCounts cc = mi_counts(on ? n11s[q] : 0, on ? A.v : 0,
-                                                          on ? cv[c + q].v : 0, P);
+                                                          on ? cvf[c + q].v : 0, P);
                             t[q][0] = on ? nlog2n(cc.n11, P) : 0.0;
                             t[q][1] = on ? nlog2n(cc.n00, P) : 0.0;
                             t[q][2] = on ? nlog2n(cc.n10, P) : 0.0;
                             t[q][3] = on ? nlog2n(cc.n01, P) : 0.0;
                         }
-                        const double Tm = nlog2n(P.m, P);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             if ((need >> q) & 1u) {
                                 const double sum = (t[q][0] + t[q][1]) + (t[q][2] + t[q][3]);
-                                const double r = sum + (Tm - (A.h + cv[c + q].h));
+                                const double r = sum + (A.h + cvh[c + q]);
                                 v[q] = fmaxf(static_cast<float>(r) * P.inv_m, 0.f);
                             }
                         }

@@ -22,8 +22,8 @@
 //
 // FP64 combine (optional, GBMI_OPT_FIXUP): pairs whose FP32 value is below
 // 1e-4 are recomputed from a table T[k] = k*log2(k) in FP64 (additions only):
-//   m*MI = T[n11] + T[n10] + T[n01] + T[n00] - H_i - H_j + T[m],
-//   H_i = T[v_i] + T[m - v_i],
+//   m*MI = T[n11] + T[n10] + T[n01] + T[n00] + K_i + K_j,
+//   K_i = T[m] / 2 - T[v_i] - T[m - v_i]  (per variable, MiVar.h),
 // which follows from Eq. 1 by expanding the logarithm of the ratio.  Pairs go
 // there without the FP32 evaluation when the chi-square bound already places
 // them below 1e-4: MI (nats) <= chi^2-divergence = det^2 / (v_i (m - v_i)
@@ -56,7 +56,7 @@ struct __align__(16) MiVar {
     float r1;      // 1 / v            (0 if v == 0)
     float r0;      // 1 / (m - v)      (0 if v == m)
     float rchi;    // 1 / (v (m - v))  (0 if either is 0)
-    double h;      // T[v] + T[m - v] for the FP64 combine (0 when it is off)
+    double h;      // T[m] / 2 - T[v] - T[m - v] for the FP64 combine (0 when it is off)
     double unused;
 };
 
@@ -97,7 +97,9 @@ __device__ __forceinline__ MiVar mi_var(int32_t v, const MiParams& P) {
     r.r1 = v > 0 ? 1.0f / a1 : 0.f;
     r.r0 = v < P.m ? 1.0f / a0 : 0.f;
     r.rchi = r.r1 * r.r0;
-    r.h = P.fixup ? nlog2n(v, P) + nlog2n(static_cast<int64_t>(P.m) - v, P) : 0.0;
+    r.h = P.fixup ? 0.5 * nlog2n(P.m, P) -
+                        (nlog2n(v, P) + nlog2n(static_cast<int64_t>(P.m) - v, P))
+                  : 0.0;
     r.unused = 0.0;
     return r;
 }
@@ -149,7 +151,8 @@ __device__ __forceinline__ MiCounts mi_counts(int32_t n11, int32_t vi, int32_t v
 }
 
 // True when the chi-square bound places the pair below the FP64 threshold.
-__device__ __forceinline__ bool mi_surely_small(float fdet, const MiVar& A, const MiVar& B,
+template <class VA, class VB>
+__device__ __forceinline__ bool mi_surely_small(float fdet, const VA& A, const VB& B,
                                                 const MiParams& P) {
     return (fdet * fdet) * (A.rchi * B.rchi) < P.chi_below;
 }
@@ -171,7 +174,7 @@ __device__ __forceinline__ float mi_fp32(const MiCounts& c, float fdet, const VA
 __device__ __forceinline__ float mi_fp64(const MiCounts& c, const MiVar& A, const MiVar& B,
                                          const MiParams& P) {
     const double s = (nlog2n(c.n11, P) + nlog2n(c.n00, P)) + (nlog2n(c.n10, P) + nlog2n(c.n01, P));
-    const double r = s + (nlog2n(P.m, P) - (A.h + B.h));
+    const double r = s + (A.h + B.h);
     return static_cast<float>(r) * P.inv_m;
 }
 
