@@ -18,8 +18,10 @@ end-to-end figure through the host-buffer C-ABI call, the FP64 oracle
 timed on the host cores on a bounded sample of pairs, the batching workload
 (512 uneven datasets in one grouped graph vs separate calls) and the serving
 workload (Poisson arrivals at 200 req/s of mixed all-pairs / cross requests
-through the native server under a 40 GB budget: p50/p99 latency, and the
-capacity of a burst of requests under continuous batching), the out-of-core
+through the native server under a 40 GB budget: p50/p99 latency, a sweep of
+offered rates up to saturation, requests whose inputs are uploaded from pinned
+host memory, and the capacity of a burst of requests under continuous
+batching), the out-of-core
 output (n = 50,000 in row panels to host memory), the sparse (CSR) path at
 99-99.9% zeros, cross MI between X and a second matrix of the same shape,
 and the precision configuration (2^20 samples x 2^14 variables: throughput
@@ -551,11 +553,13 @@ def measure_cross(dev, X, reps=5, seed=8, check_pairs=256, use_oracle=True):
 
 
 # --------------------------------------------------------------- precision configuration
-def measure_precision(dev, reps=3, check_pairs=256, use_oracle=True):
+def measure_precision(dev, reps=3, check_cols=448, use_oracle=True):
     """All-pairs MI at 2^20 samples x 2^14 variables (one Gram launch: 2^20 < 2^24),
-    p_j ~ U(0.02, 0.5): fused throughput, tensor rate, and the largest |dMI| on seeded
-    sampled pairs against the FP64 oracle (the sampled columns are gathered on the device
-    and only they are copied to the host)."""
+    p_j ~ U(0.02, 0.5), with FP4 operands (the default) and FP8 operands: throughput,
+    tensor rate, whether the two forms agree bit for bit on the whole matrix, and the
+    largest |dMI| against the FP64 oracle on every pair among `check_cols` seeded
+    columns (448 columns: 100,576 pairs with the diagonal; only those columns are
+    copied to the host)."""
     import torch
 
     import simdata
@@ -563,41 +567,59 @@ def measure_precision(dev, reps=3, check_pairs=256, use_oracle=True):
     r = simdata.PRECISION
     X, _ = simdata.from_recipe(r, device=str(dev))
     m, n = r.m, r.n
-    out = torch.empty((n, n), dtype=torch.float32, device=dev)
-    gbmi.mi_all_pairs(X, out=out, path="fused")
-    gbmi.sync()
+    pairs = n * (n - 1) // 2
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         uuid = None
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(uuid) as clocks:
-        e0.record()
-        for _ in range(reps):
+
+    def run(fp4):
+        gbmi.set_option(gbmi.OPT_FP4, 1 if fp4 else 0)
+        try:
+            out = torch.empty((n, n), dtype=torch.float32, device=dev)
             gbmi.mi_all_pairs(X, out=out, path="fused")
-        e1.record()
-        torch.cuda.synchronize(dev)
-    gbmi.sync()
-    ms = e0.elapsed_time(e1) / reps
-    pairs = n * (n - 1) // 2
-    res = {"m": m, "n": n, "dist": "p_j ~ U(0.02, 0.5), iid Bernoulli", "ms_per_step": ms,
-           "clocks": clocks.summary(),
-           "pairs_per_s": pairs / (ms * 1e-3),
-           "tflops_step": float(m) * n * n / (ms * 1e-3) / 1e12}
+            gbmi.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with ClockSampler(uuid) as clocks:
+                e0.record()
+                for _ in range(reps):
+                    gbmi.mi_all_pairs(X, out=out, path="fused")
+                e1.record()
+                torch.cuda.synchronize(dev)
+            gbmi.sync()
+        finally:
+            gbmi.set_option(gbmi.OPT_FP4, 1)
+        ms = e0.elapsed_time(e1) / reps
+        return out, {"ms_per_step": ms, "clocks": clocks.summary(),
+                     "pairs_per_s": pairs / (ms * 1e-3),
+                     "tflops_step": float(m) * n * n / (ms * 1e-3) / 1e12}
+
+    out4, fp4 = run(True)
+    out8, fp8 = run(False)
+    same = bool(torch.equal(out4, out8))
+    res = dict(m=m, n=n, dist="p_j ~ U(0.02, 0.5), iid Bernoulli", **fp4)
+    res["fp8_operands"] = fp8
+    res["fp4_fp8_whole_matrix_bit_identical"] = same
     if use_oracle:
         import oracle
-        pi, pj = simdata.sample_pairs(n, n, check_pairs, 31)
-        pi = np.concatenate([pi, np.arange(0, n, n // 16)])      # a few diagonal entries
-        pj = np.concatenate([pj, np.arange(0, n, n // 16)])
-        cols, inv = np.unique(np.concatenate([pi, pj]), return_inverse=True)
+        cols = np.sort(np.random.Generator(np.random.PCG64([r.seed, 17])).choice(
+            n, check_cols, replace=False)).astype(np.int64)
         sub = X[:, torch.from_numpy(cols).to(dev)].cpu().numpy()
-        _, want = oracle.mi_pairs(sub, inv[:len(pi)], inv[len(pi):])
-        got = out[torch.from_numpy(pi).to(dev), torch.from_numpy(pj).to(dev)].double().cpu()
-        err = float(np.max(np.abs(got.numpy() - want)))
-        res["parity"] = {"pairs": int(len(pi)), "max_abs_err_vs_oracle": err,
-                         "tolerance": 1e-6, "ok": err <= 1e-6}
-    del X, out
+        iu, ju = np.triu_indices(len(cols))
+        t0 = time.perf_counter()
+        _, want = oracle.mi_pairs(sub, iu.astype(np.int64), ju.astype(np.int64))
+        oracle_s = time.perf_counter() - t0
+        ti, tj = torch.from_numpy(cols[iu]).to(dev), torch.from_numpy(cols[ju]).to(dev)
+        got = out4[ti, tj].double().cpu().numpy()
+        err = float(np.max(np.abs(got - want)))
+        err8 = float(np.max(np.abs(out8[ti, tj].double().cpu().numpy() - want)))
+        res["parity"] = {"pairs": int(len(iu)), "columns": int(len(cols)),
+                         "max_abs_err_vs_oracle": err, "tolerance": 1e-6,
+                         "fp8_max_abs_err_vs_oracle": err8,
+                         "ok": err <= 1e-6 and err8 <= 1e-6,
+                         "oracle_s": oracle_s, "oracle_threads": oracle.max_threads()}
+    del X, out4, out8
     torch.cuda.empty_cache()
     return res
 
@@ -675,14 +697,18 @@ def _beta_matrix(m, n, g, rng, dev):
     return X
 
 
-def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burst=400, check=20):
+def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burst=400, check=20,
+                    sweep_rates=(1000.0, 3000.0, 6000.0), sweep_seconds=5.0, host_seconds=10.0):
     """Poisson arrivals of mixed all-pairs / cross requests through the native server.
 
     Each request registers its dataset(s) from a pool of resident inputs
     (so the server packs them for that request), submits, and removes them
     (dropped once the request is done); a collector waits for the tickets in
     order and releases the outputs.  Latency is submit -> completion, timed
-    inside the server.
+    inside the server, and arrival -> result, timed by the client.  After the
+    main window: shorter windows at higher offered rates (the sweep), and one
+    at the main rate whose requests upload their inputs from pinned host
+    memory before registering them.
     """
     import torch
 
@@ -696,8 +722,12 @@ def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burs
                   for m, a, b in cross]
     torch.cuda.synchronize(dev)
 
-    def run(srv, arrivals, picks, keep=0):
-        tickets, kept, errors = [], [], []
+    upload_stream = torch.cuda.Stream(dev)
+
+    def run(srv, arrivals, picks, keep=0, host=None):
+        # host: pinned host copies of the pool (index -> tensors); each request
+        # then uploads its input(s) before registering them
+        tickets, kept, errors, client_ms = [], [], [], []
         done = threading.Event()
 
         def collector():
@@ -708,14 +738,21 @@ def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burs
                         if done.is_set() and k >= len(tickets):
                             return
                         time.sleep(0.0002)
-                    t, req = tickets[k]
+                    t, req, t_arr = tickets[k]
                     out, _ = srv.wait(t, timeout_ms=120_000)
+                    client_ms.append((time.perf_counter() - t_arr) * 1e3)
                     if k < keep:
                         kept.append((req, out.clone()))
                     srv.release(t)
                     k += 1
             except Exception as e:  # reported by the caller
                 errors.append(e)
+
+        def upload(Xh):
+            with torch.cuda.stream(upload_stream):
+                Xd = Xh.to(dev, non_blocking=True)
+            upload_stream.synchronize()
+            return Xd
 
         th = threading.Thread(target=collector)
         th.start()
@@ -725,25 +762,29 @@ def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burs
                 d = t0 + at - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
+                t_arr = time.perf_counter()
                 kind, j = req
                 if kind == "all":
-                    a = srv.add_dataset(pool_all[j])
+                    Xa = upload(host[0][j]) if host else pool_all[j]
+                    a = srv.add_dataset(Xa)
                     t = srv.submit(a)
                     srv.remove_dataset(a)
                 else:
-                    a = srv.add_dataset(pool_cross[j][0])
-                    b = srv.add_dataset(pool_cross[j][1])
+                    Xa, Xb = (upload(host[1][j][0]), upload(host[1][j][1])) if host \
+                        else pool_cross[j]
+                    a = srv.add_dataset(Xa)
+                    b = srv.add_dataset(Xb)
                     t = srv.submit(a, b)
                     srv.remove_dataset(a)
                     srv.remove_dataset(b)
-                tickets.append((t, req))
+                tickets.append((t, req, t_arr))
         finally:
             done.set()
             th.join()
         wall = time.perf_counter() - t0
         if errors:
             raise errors[0]
-        return wall, kept
+        return wall, kept, client_ms
 
     def pairs_of(req):
         kind, j = req
@@ -768,7 +809,7 @@ def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burs
     arrivals = arrivals[arrivals < seconds]
     picks = picks_for(len(arrivals), r)
     with gbmi.Server(budget, max_batch=64, device=dev) as srv:
-        wall, kept = run(srv, arrivals, picks, keep=check)
+        wall, kept, cms = run(srv, arrivals, picks, keep=check)
         st = srv.stats()
     same = True
     for (kind, j), got in kept:
@@ -783,17 +824,76 @@ def measure_serving(dev, seconds=60.0, rate=200.0, budget=40 << 30, seed=5, burs
                "max_ms": st["max_ms"], "completed": int(st["completed"]),
                "batches": int(st["batches"]), "requests_per_batch": st["requests_per_batch"],
                "bit_identical_to_single_calls": f"{len(kept)} of {len(kept)} checked" if same
-               else "MISMATCH"}
+               else "MISMATCH",
+               "client_p50_ms": float(np.percentile(cms, 50)) if cms else None,
+               "client_p99_ms": float(np.percentile(cms, 99)) if cms else None}
+
+    # offered-rate sweep: shorter windows at rates up to saturation
+    sweep = []
+    for srate in sweep_rates:
+        sr = np.random.Generator(np.random.PCG64(seed + 10 + int(srate)))
+        sa = np.cumsum(sr.exponential(1.0 / srate, size=int(srate * sweep_seconds * 1.5) + 16))
+        sa = sa[sa < sweep_seconds]
+        sp = picks_for(len(sa), sr)
+        with gbmi.Server(budget, max_batch=64, device=dev) as srv:
+            sw, skept, scms = run(srv, sa, sp, keep=check)
+            sst = srv.stats()
+        ssame = True
+        for (kind, j), got in skept:
+            want = (gbmi.mi_all_pairs(pool_all[j], path="fused") if kind == "all"
+                    else gbmi.mi_cross(pool_cross[j][0], pool_cross[j][1], path="fused"))
+            gbmi.sync()
+            ssame = ssame and bool(torch.equal(got, want))
+        sweep.append({"offered_req_per_s": srate, "seconds": sweep_seconds,
+                      "requests": len(sa), "completed_req_per_s": len(sa) / sw,
+                      "pairs_per_s": sum(pairs_of(q) for q in sp) / sw,
+                      "p50_ms": sst["p50_ms"], "p99_ms": sst["p99_ms"],
+                      "client_p50_ms": float(np.percentile(scms, 50)) if scms else None,
+                      "client_p99_ms": float(np.percentile(scms, 99)) if scms else None,
+                      "batches": int(sst["batches"]),
+                      "requests_per_batch": sst["requests_per_batch"],
+                      "bit_identical_to_single_calls": ssame})
+
+    # requests whose inputs come from pinned host memory: each is uploaded (its own
+    # copy stream) and registered on arrival, so the latency includes the upload
+    host_all = [X.cpu().pin_memory() for X in pool_all]
+    host_cross = [(A.cpu().pin_memory(), B.cpu().pin_memory()) for A, B in pool_cross]
+    hr = np.random.Generator(np.random.PCG64(seed + 3))
+    ha = np.cumsum(hr.exponential(1.0 / rate, size=int(rate * host_seconds * 1.5) + 16))
+    ha = ha[ha < host_seconds]
+    hp = picks_for(len(ha), hr)
+    with gbmi.Server(budget, max_batch=64, device=dev) as srv:
+        hw, hkept, hcms = run(srv, ha, hp, keep=check, host=(host_all, host_cross))
+        hst = srv.stats()
+    hsame = True
+    for (kind, j), got in hkept:
+        want = (gbmi.mi_all_pairs(pool_all[j], path="fused") if kind == "all"
+                else gbmi.mi_cross(pool_cross[j][0], pool_cross[j][1], path="fused"))
+        gbmi.sync()
+        hsame = hsame and bool(torch.equal(got, want))
+    host_upload = {"offered_req_per_s": rate, "seconds": host_seconds, "requests": len(ha),
+                   "upload": "pinned host -> device copy per request (its own stream), then "
+                             "registration and submit",
+                   "h2d_bytes": int(sum(pool_all[j].numel() if k == "all" else
+                                        pool_cross[j][0].numel() + pool_cross[j][1].numel()
+                                        for k, j in hp)),
+                   "client_p50_ms": float(np.percentile(hcms, 50)) if hcms else None,
+                   "client_p99_ms": float(np.percentile(hcms, 99)) if hcms else None,
+                   "server_p50_ms": hst["p50_ms"], "server_p99_ms": hst["p99_ms"],
+                   "bit_identical_to_single_calls": hsame}
+    del host_all, host_cross
     # closed loop: `burst` requests submitted at once (capacity under continuous batching)
     bpicks = picks_for(burst, r)
     with gbmi.Server(budget, max_batch=64, device=dev) as srv:
-        bwall, _ = run(srv, np.zeros(burst), bpicks)
+        bwall, _, _ = run(srv, np.zeros(burst), bpicks)
         bst = srv.stats()
     bpairs = sum(pairs_of(q) for q in bpicks)
     res = {"budget_bytes": budget, "mix": "50% all-pairs m in [1e3,5e5] n in [100,8000], "
            "50% cross n1,n2 in [100,4000], log-uniform; pool of "
            f"{len(alls)} + {len(cross)} resident inputs, densities Beta(0.5,5)",
-           "poisson": poisson,
+           "poisson": poisson, "sweep": sweep, "host_upload": host_upload,
+           "latency_note": "p50/p99 are the server's submit -> completion times; client_* "
+                           "are arrival -> result in hand, measured by the client",
            "burst": {"requests": burst, "wall_s": bwall, "req_per_s": burst / bwall,
                      "pairs_per_s": bpairs / bwall, "p50_ms": bst["p50_ms"],
                      "p99_ms": bst["p99_ms"], "batches": int(bst["batches"]),
@@ -911,7 +1011,8 @@ def run_ours(args):
     fix_default = 0
     gbmi.set_option(gbmi.OPT_FIXUP, 1 - fix_default)
     try:
-        alt = timed("fused", max(3, min(args.steps, 20)), 2)
+        alt = timed("fused", max(3, min(args.steps, 20)), 2, profile=True)
+        alt_plain = timed("plain", max(3, min(args.steps, 20)), 2, profile=True)
     finally:
         gbmi.set_option(gbmi.OPT_FIXUP, fix_default)
     # the fused path with FP8 operands (the FP4 form is the default)
@@ -923,6 +1024,10 @@ def run_ours(args):
 
     # roofline of the dominant kernel (tensor-bound): m*n^2/2 MACs = m*n^2 flops per launch
     peaks = _peaks()
+    # the measured tensor-core rate of the Gram's own MMA forms (shared-memory operands,
+    # no global traffic): FP4 256 x 240 x 64 and FP8 256 x 256 x 32 on CTA pairs
+    probe4 = max(gbmi.mma_peak(1, 1, 240, 1 << 15)["flops_per_s"] for _ in range(3)) / 1e12
+    probe8 = max(gbmi.mma_peak(0, 1, 256, 1 << 14)["flops_per_s"] for _ in range(3)) / 1e12
     gram = prof.get("gram_tc_fused_mi", {"ms": float("nan"), "launches": 1})
     gram_ms = gram["ms"] / max(gram["launches"], 1)
     flops = float(m) * n * n / (world if strong else 1)   # a shard's launch does its share
@@ -937,6 +1042,8 @@ def run_ours(args):
     words = (m + 31) // 32
     popc_rate = pairs * words / (popc["ms"] * 1e-3)
     popc_peak = sm_count * POPC_PER_CLK_PER_SM * clk_mhz * 1e6
+    g8 = (fp8["profile"] or {}).get("gram_tc_fused_mi")
+    fp8_tf = flops / (g8["ms"] / max(g8["launches"], 1) * 1e-3) / 1e12 if g8 else None
     step_total = sum(v["ms"] for v in prof.values())
     kernels = {k: {"ms_per_launch": v["ms"] / max(v["launches"], 1),
                    "launches": v["launches"],
@@ -1016,9 +1123,22 @@ def run_ours(args):
                               for k, v in (plain["profile"] or {}).items()}},
         "fixup_toggled": {"fp64_combine": bool(1 - fix_default),
                           "value": job_rate(reduce_max(alt["ms"])),
-                          "ms_per_step": reduce_max(alt["ms"])},
+                          "ms_per_step": reduce_max(alt["ms"]),
+                          "over_default": reduce_max(alt["ms"]) / fused_ms,
+                          "kernels": {k: v["ms"] / max(v["launches"], 1)
+                                      for k, v in (alt["profile"] or {}).items()},
+                          "plain": {"value": job_rate(reduce_max(alt_plain["ms"])),
+                                    "ms_per_step": reduce_max(alt_plain["ms"]),
+                                    "kernels": {k: v["ms"] / max(v["launches"], 1)
+                                                for k, v in (alt_plain["profile"] or {}).items()}},
+                          "fused_over_plain": reduce_max(alt_plain["ms"]) /
+                                              reduce_max(alt["ms"])},
         "fp8_operands": {"value": job_rate(reduce_max(fp8["ms"])),
                          "ms_per_step": reduce_max(fp8["ms"]),
+                         "gram_tflops": fp8_tf, "peak_probe": probe8,
+                         "frac_of_probe": fp8_tf / probe8 if fp8_tf else None,
+                         "frac_of_bf16x2": fp8_tf / (2.0 * peaks["bf16_tflops"]) if fp8_tf
+                         else None,
                          "arithmetic": "FP8 E4M3 0/1 operands, kind::f8f6f4 MMA, 256 x 256 "
                                        "pair tiles",
                          "kernels": {k: v["ms"] / max(v["launches"], 1)
@@ -1038,6 +1158,10 @@ def run_ours(args):
                      "peak_source": f"{peaks['source']} bf16 burst x {FP4_OVER_BF16:g} "
                                     "(FP4/BF16 nominal dense ratio)",
                      "flops_per_launch": flops, "ms_per_launch": gram_ms,
+                     "peak_probe": probe4, "frac_of_probe": achieved / probe4,
+                     "probe_source": "gbmi_mma_peak: tcgen05.mma kind::mxf4 256 x 240 x 64 on "
+                                     "CTA pairs, operands resident in shared memory, every SM, "
+                                     "best of 3 (this run)",
                      "context_cublas_fp8_tflops": cublas_fp8,
                      "achieved_over_cublas_fp8": achieved / cublas_fp8 if cublas_fp8 else None,
                      "traffic_source": tsrc},

@@ -81,14 +81,20 @@ __global__ void slice_sum_kernel(const int32_t* N11, int64_t ld_n11, int slices,
 // Symmetric counts (all pairs of one matrix): only tiles with I <= J of 32 x 32
 // pairs are evaluated; each value is written to (i, j) directly and to (j, i)
 // through a shared-memory transpose, so both writes are coalesced rows.  A
-// diagonal tile evaluates its 32 x 32 pairs itself.
+// diagonal tile evaluates its 32 x 32 pairs itself.  The 32 row terms of a
+// tile are staged in shared memory once, and each thread issues the count
+// loads of its four pairs before any arithmetic, so the loads are in flight
+// together (the kernel streams 4 bytes in and 8 bytes out per pair).
 constexpr int kSymTile = 32;
 
+template <bool kFix>
 __global__ void __launch_bounds__(256)
 mi_from_counts_sym_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* vars, int64_t n,
                           const MiParams P, float* out, int64_t ld_out, int64_t tiles_per_side,
                           int upper_only, int slices, int64_t stride) {
     __shared__ float T[kSymTile][kSymTile + 1];
+    __shared__ MiVarF As[kSymTile];
+    __shared__ double Ah[kSymTile];
     // tile index -> (I, J) with I <= J, row-major over the upper triangle
     // first tile of row I: S(I) = I * tps - I (I - 1) / 2; take the largest I
     // with S(I) <= t (closed form, then exact integer correction)
@@ -101,19 +107,30 @@ mi_from_counts_sym_kernel(const int32_t* N11, int64_t ld_n11, const MiVar* vars,
     const int64_t J = I + (t - first(I));
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
     const int64_t j = J * kSymTile + tx;
-    MiVar B;
     const bool jok = j < n;
-    if (jok) B = load_var(vars + j);
+    if (ty == 0) {
+        const int64_t ia = I * kSymTile + tx;
+        As[tx] = ia < n ? load_var_f(vars + ia) : MiVarF{0, 0.f, 0.f, 0.f};
+        if (kFix) Ah[tx] = ia < n ? __ldg(&vars[ia].h) : 0.0;
+    }
+    const MiVarF B = jok ? load_var_f(vars + j) : MiVarF{0, 0.f, 0.f, 0.f};
+    const double Bh = kFix && jok ? __ldg(&vars[j].h) : 0.0;
+    int32_t cnt[kSymTile / 8];
+#pragma unroll
+    for (int k = 0; k < kSymTile / 8; ++k) {
+        const int64_t i = I * kSymTile + ty + 8 * k;
+        // upper_only: only N11[a][b], a <= b, is filled
+        const int64_t lo = (upper_only && i > j) ? j : i, hi = (upper_only && i > j) ? i : j;
+        cnt[k] = jok && i < n ? slice_sum(N11, lo * ld_n11 + hi, slices, stride) : 0;
+    }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSymTile / 8; ++k) {
         const int r = ty + 8 * k;
         const int64_t i = I * kSymTile + r;
         float v = 0.f;
         if (jok && i < n) {
-            const MiVar A = load_var(vars + i);
-            // upper_only: only N11[a][b], a <= b, is filled
-            const int64_t lo = (upper_only && i > j) ? j : i, hi = (upper_only && i > j) ? i : j;
-            v = mi_pair(slice_sum(N11, lo * ld_n11 + hi, slices, stride), A, B, P);
+            v = mi_pair_f(cnt[k], As[r], kFix ? Ah[r] : 0.0, B, Bh, P);
             out[i * ld_out + j] = v;
         }
         T[r][tx] = v;
@@ -140,8 +157,12 @@ cudaError_t launch_mi_from_counts_sym(const int32_t* N11, int64_t ld_n11, const 
     const int64_t tps = (n + kSymTile - 1) / kSymTile;
     const int64_t tiles = tps * (tps + 1) / 2;
     if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
-    mi_from_counts_sym_kernel<<<static_cast<unsigned>(tiles), 256, 0, s>>>(
-        N11, ld_n11, vars, n, P, out, ld_out, tps, upper_only, slices, slice_stride);
+    if (P.fixup)
+        mi_from_counts_sym_kernel<true><<<static_cast<unsigned>(tiles), 256, 0, s>>>(
+            N11, ld_n11, vars, n, P, out, ld_out, tps, upper_only, slices, slice_stride);
+    else
+        mi_from_counts_sym_kernel<false><<<static_cast<unsigned>(tiles), 256, 0, s>>>(
+            N11, ld_n11, vars, n, P, out, ld_out, tps, upper_only, slices, slice_stride);
     return cudaGetLastError();
 }
 

@@ -178,8 +178,10 @@ __device__ __forceinline__ float mi_fp64(const MiCounts& c, const MiVar& A, cons
     return static_cast<float>(r) * P.inv_m;
 }
 
-__device__ __forceinline__ float mi_pair(int32_t n11, const MiVar& A, const MiVar& B,
-                                         const MiParams& P) {
+// MI of one pair from its co-occurrence count, the FP32 terms of both
+// variables and (FP64 combine) their FP64 terms Ah, Bh (MiVar.h).
+__device__ __forceinline__ float mi_pair_f(int32_t n11, const MiVarF& A, double Ah,
+                                           const MiVarF& B, double Bh, const MiParams& P) {
     const MiCounts c = mi_counts(n11, A.v, B.v, P);
     if (c.det == 0) return 0.f;   // exact independence: every log ratio is 0
     const float fdet = static_cast<float>(c.det);
@@ -189,8 +191,18 @@ __device__ __forceinline__ float mi_pair(int32_t n11, const MiVar& A, const MiVa
         mi = mi_fp32(c, fdet, A, B, P);
         need64 = P.fixup && mi < P.fixup_below;
     }
-    if (need64) mi = mi_fp64(c, A, B, P);
+    if (need64) {
+        const double s = (nlog2n(c.n11, P) + nlog2n(c.n00, P)) +
+                         (nlog2n(c.n10, P) + nlog2n(c.n01, P));
+        mi = static_cast<float>(s + (Ah + Bh)) * P.inv_m;
+    }
     return fmaxf(mi, 0.f);
+}
+
+__device__ __forceinline__ float mi_pair(int32_t n11, const MiVar& A, const MiVar& B,
+                                         const MiParams& P) {
+    return mi_pair_f(n11, MiVarF{A.v, A.r1, A.r0, A.rchi}, A.h, MiVarF{B.v, B.r1, B.r0, B.rchi},
+                     B.h, P);
 }
 
 }  // namespace gbmi

@@ -7,8 +7,9 @@ every count of the tensor-core Gram equals the popcount Gram's; 20,000
 seeded pairs, all planted pairs and 500 diagonal entries against the FP64
 oracle (MI within 1e-6, counts exact); symmetry of the whole matrix.
 
-precision (m=2^20, n=2^14): full tensor-core vs popcount count equality;
-MI on every pair among 300 seeded columns against the oracle.
+precision (m=2^20, n=2^14): full tensor-core vs popcount count equality with
+FP4 and with FP8 operands; MI on every pair among 448 seeded columns (100,576
+pairs) against the oracle, and the two operand forms' MI matrices bit-identical.
 """
 from __future__ import annotations
 
@@ -65,25 +66,39 @@ def test_paper_scale_sampled_parity():
     print(f"paper scale: max |MI - oracle| over {len(pi)} pairs = {err:.3e}")
 
 
-def test_precision_config_counts_and_sampled_mi():
+@pytest.fixture
+def _fp4_restored():
+    yield
+    gbmi.set_option(gbmi.OPT_FP4, 1)
+
+
+def test_precision_config_counts_and_sampled_mi(_fp4_restored):
     r = simdata.PRECISION
     X, _ = simdata.from_recipe(r, device="cuda")
-    tc = gbmi.counts_all_pairs(X, path="plain")
     pc = gbmi.counts_all_pairs(X, path="popcount")
-    gbmi.sync()
-    assert torch.equal(tc, pc), "tensor-core and popcount counts differ at m=2^20"
-    del pc
-    out = gbmi.mi_all_pairs(X)
-    gbmi.sync()
-    cols = np.sort(np.random.default_rng(7).choice(r.n, 300, replace=False)).astype(np.int64)
+    outs = {}
+    for fp4 in (1, 0):
+        gbmi.set_option(gbmi.OPT_FP4, fp4)
+        tc = gbmi.counts_all_pairs(X, path="plain")
+        gbmi.sync()
+        assert torch.equal(tc, pc), f"tensor-core (fp4={fp4}) and popcount counts differ at m=2^20"
+        del tc
+        outs[fp4] = gbmi.mi_all_pairs(X)
+        gbmi.sync()
+    gbmi.set_option(gbmi.OPT_FP4, 1)
+    assert torch.equal(outs[1], outs[0]), "FP4 and FP8 operands give different MI"
+    out = outs[1]
+    del outs
+    cols = np.sort(np.random.default_rng(7).choice(r.n, 448, replace=False)).astype(np.int64)
     sub = X[:, torch.from_numpy(cols).cuda()].cpu().numpy()
     XT = oracle.transpose(sub)
     iu, ju = np.triu_indices(len(cols))
+    assert len(iu) >= 100_000
     counts, want = oracle.mi_pairs_t(XT, XT, iu.astype(np.int64), ju.astype(np.int64))
     ti = torch.from_numpy(cols[iu]).cuda()
     tj = torch.from_numpy(cols[ju]).cuda()
     got = out[ti, tj].double().cpu().numpy()
     assert np.abs(got - want).max() <= 1e-6
-    assert np.array_equal(tc[ti, tj].cpu().numpy().astype(np.int64), counts[:, 0])
+    assert np.array_equal(pc[ti, tj].cpu().numpy().astype(np.int64), counts[:, 0])
     print(f"precision config: max |MI - oracle| over {len(iu)} pairs = "
           f"{np.abs(got - want).max():.3e}")
