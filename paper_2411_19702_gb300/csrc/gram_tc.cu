@@ -203,6 +203,17 @@ __device__ __forceinline__ int tile_n(const GramJob& job, const GramTile& tile) 
     return n < 32 ? 32 : (n > job.bn ? job.bn : n);
 }
 
+// Columns [0, c0) of a tile of a symmetric job lie below the diagonal for all
+// of its rows (tile rows start at tile_m I, its columns at bn J): its MMAs and
+// B copies start at column c0, a multiple of 32, and accumulator column a holds
+// tile column c0 + a.  0 for cross jobs and direct operands.
+__device__ __forceinline__ int tile_c0(const GramJob& job, const GramTile& tile, int tile_m,
+                                       bool direct) {
+    if (job.symmetric == 0 || direct) return 0;
+    const int64_t skip = static_cast<int64_t>(tile.I) * tile_m - static_cast<int64_t>(tile.J) * job.bn;
+    return skip > 0 ? static_cast<int>(skip & ~int64_t{31}) : 0;
+}
+
 // K blocks [kb0, kb1) of the job that a tile accumulates: all of them, or its
 // part's share for a split tile.
 __device__ __forceinline__ void tile_krange(const GramJob& job, const GramTile& tile, int& kb0,
@@ -280,13 +291,14 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
                                                                                : &maps.box64);
         // pair: the partner CTA holds B rows [N/2, N) of the tile's MMA width N;
         // each CTA's half is one box of 120 rows when N = 240, else of 128
-        const int nhalf = kPair ? tile_n(job, tile) / 2 : 0;
+        const int c0 = tile_c0(job, tile, Plan<kPair>::tile_m, L.direct != 0);
+        const int nhalf = kPair ? (tile_n(job, tile) - c0) / 2 : 0;
         const bool half120 = kPair && nhalf == 120;
         const CUtensorMap* mapH = half120 ? &maps.box120 : &maps.box128;
         const uint32_t bytes = static_cast<uint32_t>(
             (Plan<kPair>::tile_m + (kPair ? (half120 ? 240 : 2 * kTcBM) : brows)) * kTcBK);
         const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m;
-        const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn;
+        const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn + c0;
         if (L.direct && ((a0 | b0) & 15) != 0) {
             // a direct copy's x coordinate (a variable index) must be a multiple
             // of 16 bytes: record it and issue nothing
@@ -382,7 +394,8 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
         if (t < 0) break;
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
-        const uint32_t mma_n = static_cast<uint32_t>(tile_n(job, tile));
+        const uint32_t mma_n = static_cast<uint32_t>(
+            tile_n(job, tile) - tile_c0(job, tile, Plan<kPair>::tile_m, L.direct != 0));
         const uint32_t idesc =
             kFp4 ? ptx::idesc_mxf4_f32(kPair ? 2 * kTcBM : kTcBM, mma_n)
             : kPair ? ptx::idesc_e4m3_f32(2 * kTcBM, mma_n)
@@ -584,8 +597,11 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             break;
         }
         ptx::tc_fence_after();
+        // accumulator column of tile column col_base + c: col_base + c - c0 (the
+        // epilogue reads no column below c0: those lie below the diagonal)
+        const int c0 = tile_c0(job, tile, Plan<kPair>::tile_m, L.direct != 0);
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(lane_base) << 16) +
-                               static_cast<uint32_t>(acc * kAccCols + col_base);
+                               static_cast<uint32_t>(acc * kAccCols + col_base - c0);
         if constexpr (is_mi<kMode>()) {
             // MI: chunks of 4 columns in one small loop body; the next chunk's
             // accumulator columns load from TMEM during this chunk's math.
