@@ -363,6 +363,8 @@ def measure_batch(dev, reps=3, k=512, seed=4):
     pairs = int(sum(int(n) * (int(n) - 1) // 2 for n in ns))
     t0 = time.perf_counter()
     table = autotune.tune(list(zip(ms.tolist(), ns.tolist())), reps=2)
+    # the batch-level choice: rule / per-bucket table / all single / all pairs
+    batch_choice = autotune.tune_batch(Xs, table=table, reps=2)
     tune_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
 
@@ -405,9 +407,17 @@ def measure_batch(dev, reps=3, k=512, seed=4):
            "speedup_vs_separate_fused": fused_ms / batch_ms,
            "tiles": plan.tiles, "launches_per_run": launches_per_run,
            "autotuned_buckets": len(table), "autotune_s": tune_s,
+           "autotune_choices": {k: {"tile_n": v["tile_n"], "pair": v["pair"],
+                                    "ms": {c: round(t, 4) for c, t in v["ms"].items()}}
+                                for k, v in table.items()},
+           "autotune_knobs": "per (floor(log2 m), floor(2 log2 n)) bucket: single-CTA tile "
+                             "width 64/128/256 and single-CTA vs CTA-pair kernel; per batch: "
+                             "the kernel assignment (rule / table / all single / all pairs)",
+           "batch_kernel_choice": batch_choice,
            "bit_identical_to_separate": bool(same)}
     plan.close()
     gbmi.tuner_clear()
+    gbmi.set_option(gbmi.OPT_PAIR, 1)
     del Xs, outs, sep_out
     torch.cuda.empty_cache()
     return res

@@ -388,6 +388,15 @@ gbmi_status gbmi_server_destroy(gbmi_server* srv);
 gbmi_status gbmi_tuner_set(int64_t m, int64_t n, int tile_n);
 gbmi_status gbmi_tuner_clear(void);
 int gbmi_tile_n(int64_t m, int64_t n);
+/* Kernel choice of the bucket of (m, n), measured by the autotuner: 1 = CTA
+ * pairs (256-row tiles on clusters of two SMs), 0 = single-CTA tiles of the
+ * bucket's tile width, -1 = the built-in rule (pairs when a single call fills
+ * the GPU with them; in a batch, when both sides span >= 768 variables).
+ * Applies to single calls, batches and servers created afterwards, unless
+ * GBMI_OPT_PAIR forces a kernel.  gbmi_tuner_pair returns the current choice
+ * (-1 for an untuned bucket).  Errors: GBMI_ERR_ARG. */
+gbmi_status gbmi_tuner_set_pair(int64_t m, int64_t n, int pair);
+int gbmi_tuner_pair(int64_t m, int64_t n);
 
 /* Per-kernel launch profile (enable with GBMI_OPT_PROFILE).  Each kernel
  * launch is bracketed by CUDA events on the library's stream;

@@ -1,12 +1,17 @@
-"""Tile-width autotuner for the tensor-core Gram.
+"""Autotuner for the tensor-core Gram: tile width and kernel per (m, n) bucket.
 
-The Gram works on 128 x tile_n output tiles with tile_n in {64, 128, 256}.
-Narrow tiles waste less padding when n is small; wide tiles stream fewer
-operand bytes per pair.  ``tune`` measures, for one representative shape per
-(m, n) bucket (floor(log2 m), floor(2 log2 n) -- the buckets the native table
-uses), the device time of the fused kernel with each width through the
-library's event profiler, keeps the fastest, and installs the choices with
-``gbmi_tuner_set``.  Tables are saved and loaded as JSON.
+The Gram runs either single-CTA tiles of 128 x tile_n (tile_n in {64, 128,
+256}; 240 with FP4 operands) or CTA-pair tiles of 256 x 256 (256 x 240 with
+FP4) on clusters of two SMs.  Narrow tiles waste less padding when n is
+small; wide tiles and CTA pairs stream fewer operand bytes per pair but need
+enough tiles to fill the GPU.  ``tune`` measures, for one representative
+shape per (m, n) bucket (floor(log2 m), floor(2 log2 n) -- the buckets the
+native table uses), the device time of the fused kernel for every candidate
+(each single-CTA width, and CTA pairs) through the library's event profiler,
+keeps the fastest, and installs the choice: the bucket's single-CTA width
+(``gbmi_tuner_set``) and whether it runs on CTA pairs
+(``gbmi_tuner_set_pair``).  Single calls, batches and servers then follow
+the table.  Tables are saved and loaded as JSON.
 """
 from __future__ import annotations
 
@@ -15,17 +20,18 @@ import math
 
 from . import gbmi
 
-CANDIDATES = (64, 128, 256)
+CANDIDATES = (("single", 64), ("single", 128), ("single", 256), ("pair", 0))
 
 
 def bucket(m: int, n: int) -> tuple[int, int]:
     return int(math.floor(math.log2(max(m, 1)))), int(math.floor(2.0 * math.log2(max(n, 1))))
 
 
-def _time_width(X, tile_n: int, reps: int) -> float:
+def _time_candidate(X, kind: str, tile_n: int, reps: int) -> float:
     import torch
     n = X.shape[1]
     out = torch.empty((n, n), dtype=torch.float32, device=X.device)
+    gbmi.set_option(gbmi.OPT_PAIR, 2 if kind == "pair" else 0)
     gbmi.set_option(gbmi.OPT_TILE_N, tile_n)
     try:
         gbmi.mi_all_pairs(X, out=out, path="fused")
@@ -36,15 +42,24 @@ def _time_width(X, tile_n: int, reps: int) -> float:
         prof = gbmi.profile(enable=False)
     finally:
         gbmi.set_option(gbmi.OPT_TILE_N, 0)
-    g = prof.get("gram_tc_fused_mi")
-    return g["ms"] / max(g["launches"], 1) if g else float("inf")
+        gbmi.set_option(gbmi.OPT_PAIR, 1)
+    # the Gram launches of the call (one fused launch, or the sample split's
+    # counts launch and the MI kernel that sums its parts)
+    ms = sum(v["ms"] for k, v in prof.items() if k.startswith("gram_tc") or k == "mi_from_counts")
+    calls = max((v["launches"] for k, v in prof.items() if k.startswith("gram_tc")), default=0)
+    return ms / calls if calls else float("inf")
+
+
+def _name(kind: str, tile_n: int) -> str:
+    return "pair" if kind == "pair" else f"single{tile_n}"
 
 
 def tune(shapes, candidates=CANDIDATES, reps: int = 3, density: float = 0.1, seed: int = 0,
          device: str = "cuda", install: bool = True) -> dict:
-    """Measure each candidate width on one random problem per bucket of ``shapes``.
+    """Measure each candidate on one random problem per bucket of ``shapes``.
 
-    Returns {"m,n-bucket": {"m": m, "n": n, "tile_n": best, "ms": {width: ms}}}.
+    Returns {"mb,nb": {"m": m, "n": n, "tile_n": best single-CTA width,
+    "pair": 0 or 1, "ms": {candidate: ms}}}.
     """
     import torch
     g = torch.Generator(device=device)
@@ -55,20 +70,78 @@ def tune(shapes, candidates=CANDIDATES, reps: int = 3, density: float = 0.1, see
     table = {}
     for key, (m, n) in sorted(reps_by_bucket.items()):
         X = (torch.rand((m, n), generator=g, device=device) < density).to(torch.uint8)
-        times = {w: _time_width(X, w, reps) for w in candidates}
-        best = min(times, key=lambda w: (times[w], -w))
-        table[f"{key[0]},{key[1]}"] = {"m": m, "n": n, "tile_n": best,
-                                       "ms": {str(w): t for w, t in times.items()}}
+        times = {_name(k, w): _time_candidate(X, k, w, reps) for k, w in candidates}
+        singles = {w: times[_name("single", w)] for k, w in candidates if k == "single"}
+        best_w = min(singles, key=lambda w: (singles[w], -w)) if singles else 256
+        best = min(times, key=lambda c: times[c])
+        table[f"{key[0]},{key[1]}"] = {"m": m, "n": n, "tile_n": best_w,
+                                       "pair": 1 if best == "pair" else 0, "ms": times}
         del X
     if install:
         apply(table)
     return table
 
 
+def tune_batch(Xs, Ys=None, table: dict | None = None, reps: int = 3) -> dict:
+    """Choose the kernel assignment of a grouped batch by timing the whole batch.
+
+    Candidates: the built-in rule (jobs whose both sides span >= 768 variables
+    on CTA pairs), the per-bucket ``table`` (if given), every job on
+    single-CTA tiles, every job on CTA pairs.  Each is built as a batch plan
+    (one CUDA graph) and timed with CUDA events over ``reps`` replays; the
+    fastest setting is left installed (GBMI_OPT_PAIR and the tuner table) and
+    returned with all times: {"best": name, "ms": {name: ms}}.
+    """
+    import torch
+
+    def timed(setup):
+        setup()
+        plan = gbmi.Batch(Xs, Ys)
+        try:
+            plan.run()
+            gbmi.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                plan.run()
+            e1.record()
+            e1.synchronize()
+            gbmi.sync()
+            return e0.elapsed_time(e1) / reps
+        finally:
+            plan.close()
+
+    def rule():
+        gbmi.tuner_clear()
+        gbmi.set_option(gbmi.OPT_PAIR, 1)
+
+    def with_table():
+        rule()
+        apply(table)
+
+    def single():
+        gbmi.tuner_clear()
+        gbmi.set_option(gbmi.OPT_PAIR, 0)
+
+    def pairs():
+        gbmi.tuner_clear()
+        gbmi.set_option(gbmi.OPT_PAIR, 2)
+
+    setups = {"rule": rule, "single": single, "pairs": pairs}
+    if table:
+        setups["table"] = with_table
+    times = {name: timed(f) for name, f in setups.items()}
+    best = min(times, key=lambda k: times[k])
+    setups[best]()
+    return {"best": best, "ms": times}
+
+
 def apply(table: dict):
     """Install a table's choices in the library."""
     for entry in table.values():
         gbmi.tuner_set(entry["m"], entry["n"], entry["tile_n"])
+        if "pair" in entry:
+            gbmi.tuner_set_pair(entry["m"], entry["n"], entry["pair"])
 
 
 def save(table: dict, path: str):

@@ -254,7 +254,10 @@ gbmi_status create(const gbmi_job* jobs, int k, gbmi_batch** out) {
     const bool pairs_ok = rt::g_opt.pair != 0 && c.pair_clusters > 0 && rt::g_opt.tile_n == 0;
     for (int i = 0; i < k; ++i) {
         GramJob& g = b->hgram[i];
-        if (pairs_ok && (rt::g_opt.pair == 2 || (g.n_a >= kPairMinN && g.n_b >= kPairMinN))) {
+        // a tuned bucket decides; else the size rule
+        const int tuned = rt::tuner_pair(g.mp.m, std::max<int64_t>(g.n_a, g.n_b));
+        const bool rule = g.n_a >= kPairMinN && g.n_b >= kPairMinN;
+        if (pairs_ok && (rt::g_opt.pair == 2 || (tuned >= 0 ? tuned == 1 : rule))) {
             pair_job[i] = 1;
             g.bn = bn_max;
         }

@@ -174,11 +174,13 @@ gbmi_status tail_split_list(DeviceCtx& c, int S, int parts, int* count) {
 // taken whenever its launch keeps at least as many SMs busy as the single-CTA
 // launch of the same problem would (small problems keep the finer tiles).
 // bn_max: the pair's tile width (256; 240 for FP4 operands).
-bool use_pair(const DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn,
+bool use_pair(const DeviceCtx& c, int64_t m, int64_t n_a, int64_t n_b, bool sym, int bn,
               int bn_max = kTcBNMax) {
     if (g_opt.pair == 0 || c.pair_clusters <= 0) return false;
     if (g_opt.pair == 2) return true;   // forced (tests)
     if (g_opt.tile_n != 0) return false;   // a forced tile width names a single-CTA tile
+    const int tuned = rt::tuner_pair(m, std::max(n_a, n_b));   // a tuned bucket decides
+    if (tuned >= 0) return tuned == 1;
     const int64_t pair_tiles = gram_tile_count(n_a, n_b, bn_max, sym, 2 * kTcBM);
     const int64_t single_tiles = gram_tile_count(n_a, n_b, bn, sym, kTcBM);
     const int64_t pair_sms = 2 * std::min<int64_t>(pair_tiles, c.pair_clusters);
@@ -330,7 +332,7 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     // two SMs (packed operands only)
     const int bn_max = fp4 ? kTcBNFp4 : kTcBNMax;
     const bool pair = dmaps == nullptr &&
-                      use_pair(c, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn, bn_max);
+                      use_pair(c, m, proto.n_a, proto.n_b, proto.symmetric != 0, proto.bn, bn_max);
     const int64_t spk = kb_samples(fp4);
     const int64_t kb_all = pack_ld_of(m, fp4) / spk;
     const int bn = pair ? bn_max : std::min(proto.bn, bn_max);
@@ -732,7 +734,7 @@ gbmi_status host_pipelined(DeviceCtx& c, const uint8_t* X, const uint8_t* Y, int
     // tiles in panel-major order
     const int bn_max = L.fp4 ? kTcBNFp4 : kTcBNMax;
     const int bn_single = std::min(rt::choose_bn(m, n1, n2, sym), bn_max);
-    const bool pair = use_pair(c, n1, n2, sym, bn_single, bn_max);
+    const bool pair = use_pair(c, m, n1, n2, sym, bn_single, bn_max);
     const int bm = pair ? 2 * kTcBM : kTcBM;
     const int bn = pair ? bn_max : bn_single;
     const int64_t TI = (n1 + bm - 1) / bm, TJ = (n2 + bn - 1) / bn;
@@ -1000,7 +1002,7 @@ gbmi_status blocked_impl(const uint8_t* X, const uint8_t* Y, int64_t m, int64_t 
         const int bn_max = L.fp4 ? kTcBNFp4 : kTcBNMax;
         g.bn = std::min(rt::choose_bn(m, rows, w, false), bn_max);
         if (L.direct && g.bn < kTcBM) g.bn = kTcBM;
-        if (!L.direct && use_pair(c, rows, w, false, g.bn, bn_max)) {
+        if (!L.direct && use_pair(c, m, rows, w, false, g.bn, bn_max)) {
             g.bn = bn_max;
             pair_panel[static_cast<size_t>(p)] = 1;
         }
@@ -1413,6 +1415,20 @@ gbmi_status gbmi_tuner_clear(void) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     rt::tuner_clear();
     return GBMI_OK;
+}
+
+gbmi_status gbmi_tuner_set_pair(int64_t m, int64_t n, int pair) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (m < 1 || n < 1) return fail(GBMI_ERR_ARG, "m and n must be >= 1");
+    if (pair < -1 || pair > 1) return fail(GBMI_ERR_ARG, "pair must be -1, 0 or 1");
+    rt::tuner_set_pair(m, n, pair);
+    return GBMI_OK;
+}
+
+int gbmi_tuner_pair(int64_t m, int64_t n) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (m < 1 || n < 1) return -1;
+    return rt::tuner_pair(m, n);
 }
 
 int gbmi_tile_n(int64_t m, int64_t n) {

@@ -105,7 +105,13 @@ cudaEvent_t take_event() {
 }
 
 // ---------------------------------------------------------------- tuner table
-std::map<std::pair<int, int>, int> g_tuner;
+// per (m, n) bucket: the single-CTA tile width (0: not tuned) and the kernel
+// (-1: the built-in rule, 0: single-CTA tiles, 1: CTA pairs)
+struct TunerEntry {
+    int bn = 0;
+    int pair = -1;
+};
+std::map<std::pair<int, int>, TunerEntry> g_tuner;
 
 std::pair<int, int> bucket(int64_t m, int64_t n) {
     const int mb = static_cast<int>(std::floor(std::log2(static_cast<double>(std::max<int64_t>(m, 1)))));
@@ -277,7 +283,7 @@ gbmi_status mi_params(DeviceCtx& c, int64_t m, MiParams* P) {
 int choose_bn(int64_t m, int64_t n_a, int64_t n_b, bool symmetric) {
     if (g_opt.tile_n == 64 || g_opt.tile_n == 128 || g_opt.tile_n == 256) return g_opt.tile_n;
     const auto it = g_tuner.find(bucket(m, std::max(n_a, n_b)));
-    if (it != g_tuner.end()) return it->second;
+    if (it != g_tuner.end() && it->second.bn != 0) return it->second.bn;
     // operand traffic: every tile streams 128 + bn rows for each sample block
     int best = 256;
     double best_cost = -1.0;
@@ -292,7 +298,12 @@ int choose_bn(int64_t m, int64_t n_a, int64_t n_b, bool symmetric) {
     return best;
 }
 
-void tuner_set(int64_t m, int64_t n, int bn) { g_tuner[bucket(m, n)] = bn; }
+void tuner_set(int64_t m, int64_t n, int bn) { g_tuner[bucket(m, n)].bn = bn; }
+void tuner_set_pair(int64_t m, int64_t n, int pair) { g_tuner[bucket(m, n)].pair = pair; }
+int tuner_pair(int64_t m, int64_t n) {
+    const auto it = g_tuner.find(bucket(m, n));
+    return it != g_tuner.end() ? it->second.pair : -1;
+}
 void tuner_clear() { g_tuner.clear(); }
 int tuner_size() { return static_cast<int>(g_tuner.size()); }
 

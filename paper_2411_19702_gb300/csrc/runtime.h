@@ -104,6 +104,10 @@ MiParams mi_params_plain(int64_t m, int fixup, const double* T);
 // set, else a tuner-table entry for (m, n), else the operand-traffic cost model.
 int choose_bn(int64_t m, int64_t n_a, int64_t n_b, bool symmetric);
 void tuner_set(int64_t m, int64_t n, int bn);
+// Kernel choice of the bucket of (m, n): -1 the built-in rule (untuned), 0
+// single-CTA tiles, 1 CTA pairs.
+void tuner_set_pair(int64_t m, int64_t n, int pair);
+int tuner_pair(int64_t m, int64_t n);
 void tuner_clear();
 int tuner_size();
 

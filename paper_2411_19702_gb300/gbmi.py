@@ -79,6 +79,8 @@ def load(path: str | None = None):
             "mi_all_pairs_noalloc": [vp, i64, i64, vp],
             "gbmi_mma_peak": [i32, i32, i32, i64, vp, vp],
             "gbmi_tuner_set": [i64, i64, i32],
+            "gbmi_tuner_set_pair": [i64, i64, i32],
+            "gbmi_tuner_pair": [i64, i64],
             "gbmi_tuner_clear": [],
             "gbmi_tile_n": [i64, i64],
             "gbmi_batch_create": [vp, i32, vp],
@@ -529,6 +531,15 @@ def tuner_set(m: int, n: int, tile_n: int):
 
 def tuner_clear():
     _check(load().gbmi_tuner_clear())
+
+
+def tuner_set_pair(m: int, n: int, pair: int):
+    """Kernel choice for the (m, n) bucket: 1 CTA pairs, 0 single-CTA tiles, -1 the rule."""
+    _check(load().gbmi_tuner_set_pair(int(m), int(n), int(pair)))
+
+
+def tuner_pair(m: int, n: int) -> int:
+    return int(load().gbmi_tuner_pair(int(m), int(n)))
 
 
 def tile_n(m: int, n: int) -> int:

@@ -93,17 +93,27 @@ def test_autotuner_installs_choices_and_keeps_results():
     assert len(table) == 2
     for entry in table.values():
         assert entry["tile_n"] in (64, 128, 256)
+        assert entry["pair"] in (0, 1)
+        assert set(entry["ms"]) == {"single64", "single128", "single256", "pair"}
         assert gbmi.tile_n(entry["m"], entry["n"]) == entry["tile_n"]
+        assert gbmi.tuner_pair(entry["m"], entry["n"]) == entry["pair"]
     X = _rand(4000, 96, 7)
-    got = gbmi.mi_all_pairs(X, path="fused")
+    Y = _rand(20000, 900, 8)
+    got, goty = gbmi.mi_all_pairs(X, path="fused"), gbmi.mi_all_pairs(Y, path="fused")
+    b = gbmi.Batch([X, Y])
+    bx, by = b.run()
     gbmi.set_option(gbmi.OPT_TILE_N, 256)
     try:
         ref = gbmi.mi_all_pairs(X, path="fused")
     finally:
         gbmi.set_option(gbmi.OPT_TILE_N, 0)
+    gbmi.tuner_clear()
+    refy = gbmi.mi_all_pairs(Y, path="fused")
     gbmi.sync()
     assert torch.equal(got, ref)
-    gbmi.tuner_clear()
+    assert torch.equal(goty, refy)
+    assert torch.equal(bx, ref) and torch.equal(by, refy)
+    b.close()
 
 
 def test_batch_on_cta_pairs_matches_single_calls():

@@ -45,15 +45,35 @@ def test_tuner_rejects_bad_widths():
 
 
 def test_autotune_table_round_trip(tmp_path):
-    table = {"16,26": {"m": 100_000, "n": 10_000, "tile_n": 128,
-                       "ms": {"64": 3.0, "128": 2.0, "256": 2.5}}}
+    table = {"16,26": {"m": 100_000, "n": 10_000, "tile_n": 128, "pair": 1,
+                       "ms": {"single64": 3.0, "single128": 2.0, "single256": 2.5,
+                              "pair": 1.5}},
+             "12,12": {"m": 5000, "n": 64, "tile_n": 64, "pair": 0,
+                       "ms": {"single64": 0.1, "single128": 0.2, "single256": 0.3,
+                              "pair": 0.4}}}
     path = str(tmp_path / "tune.json")
     autotune.save(table, path)
     gbmi.tuner_clear()
     got = autotune.load(path)
     assert got == table
     assert gbmi.tile_n(100_000, 10_000) == 128
+    assert gbmi.tuner_pair(100_000, 10_000) == 1
+    assert gbmi.tuner_pair(5000, 64) == 0
+    assert gbmi.tuner_pair(5000, 5000) == -1          # untuned bucket: the built-in rule
     assert autotune.bucket(100_000, 10_000) == (16, 26)
+    gbmi.tuner_clear()
+    assert gbmi.tuner_pair(100_000, 10_000) == -1
+
+
+def test_tuner_pair_argument_checks():
+    with pytest.raises(gbmi.GbmiError):
+        gbmi.tuner_set_pair(1000, 100, 2)
+    with pytest.raises(gbmi.GbmiError):
+        gbmi.tuner_set_pair(0, 100, 1)
+    gbmi.tuner_set_pair(1000, 100, 1)
+    assert gbmi.tuner_pair(1000, 100) == 1
+    gbmi.tuner_set_pair(1000, 100, -1)
+    assert gbmi.tuner_pair(1000, 100) == -1
     gbmi.tuner_clear()
 
 
