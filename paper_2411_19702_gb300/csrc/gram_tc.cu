@@ -713,7 +713,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                             const MiVarF B = cvf[c + q];
                             const MiCounts cc = mi_counts(n11, A.v, B.v, P);
                             if (cc.det != 0) {
-                                const float fdet = static_cast<float>(cc.det);
+                                const float fdet = det_to_float(cc.det);
                                 bool small = P.fixup && mi_surely_small(fdet, A, B, P);
                                 if (!small) {
                                     mi = fmaxf(mi_fp32(cc, fdet, A, B, P), 0.f);
@@ -725,7 +725,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                             const MiVarF B = cvf[c + q];
                             const MiCounts cc = mi_counts(n11, A.v, B.v, P);
                             if (cc.det != 0)
-                                mi = fmaxf(mi_fp32(cc, static_cast<float>(cc.det), A, B, P), 0.f);
+                                mi = fmaxf(mi_fp32(cc, det_to_float(cc.det), A, B, P), 0.f);
                         }
                     }
                     v[q] = mi;

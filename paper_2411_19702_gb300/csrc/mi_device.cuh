@@ -139,6 +139,18 @@ struct MiCounts {
     int64_t det;
 };
 
+// The determinant as a float from the two exact 31-bit halves of its
+// magnitude (both non-negative, so their sum does not cancel), within 1.5
+// ulp: FP32 conversions and one FMA (a 64-bit integer conversion would run on
+// the FP64 pipe, which is slow on this part).  |d| < 2^62.
+__device__ __forceinline__ float det_to_float(int64_t d) {
+    const uint64_t a = static_cast<uint64_t>(d < 0 ? -d : d);
+    const uint32_t hi = static_cast<uint32_t>(a >> 31);
+    const uint32_t lo = static_cast<uint32_t>(a) & 0x7FFFFFFFu;
+    const float f = fmaf(static_cast<float>(hi), 2147483648.0f, static_cast<float>(lo));
+    return d < 0 ? -f : f;
+}
+
 __device__ __forceinline__ MiCounts mi_counts(int32_t n11, int32_t vi, int32_t vj,
                                               const MiParams& P) {
     MiCounts c;
@@ -184,7 +196,7 @@ __device__ __forceinline__ float mi_pair_f(int32_t n11, const MiVarF& A, double 
                                            const MiVarF& B, double Bh, const MiParams& P) {
     const MiCounts c = mi_counts(n11, A.v, B.v, P);
     if (c.det == 0) return 0.f;   // exact independence: every log ratio is 0
-    const float fdet = static_cast<float>(c.det);
+    const float fdet = det_to_float(c.det);
     bool need64 = P.fixup && mi_surely_small(fdet, A, B, P);
     float mi = 0.f;
     if (!need64) {
