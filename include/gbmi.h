@@ -65,7 +65,7 @@ typedef enum {
 /* Options for gbmi_set_option.  Their defaults can also be set in the
  * environment when the library loads: GBMI_FIXUP, GBMI_TILE_N, GBMI_PAIR,
  * GBMI_DIRECT, GBMI_FP4, GBMI_TIMEOUT_NS, GBMI_GROUP_COLS, GBMI_MAX_CTAS,
- * GBMI_TAIL_SPLIT (out-of-range
+ * GBMI_TAIL_SPLIT, GBMI_TAIL_COLS (out-of-range
  * values are ignored).  GBMI_LOG=1 also writes every error text to stderr. */
 typedef enum {
     GBMI_OPT_FIXUP = 1,          /* 1: FP64 n*log2(n) combine for pairs whose FP32 MI < 1e-4 (default 0) */
@@ -106,13 +106,21 @@ typedef enum {
                                     1.0; tiles at most 240 wide): the same exact counts from half
                                     the operand bytes, about 1.7x the FP8 Gram's rate; 0: FP8
                                     operands (default 1)                                          */
-    GBMI_OPT_TAIL_SPLIT = 13     /* fused MI launch: its last (tiles mod slots) + slots tiles run
+    GBMI_OPT_TAIL_SPLIT = 13,    /* fused MI launch: its last (tiles mod slots) + slots tiles run
                                     as units of half the samples each; the second unit of a tile
                                     adds the first's exact int32 counts before the MI, so the
                                     launch ends in half-length pieces instead of a partial wave of
                                     whole tiles: 0 = off (default; at 10^5 x 10^4 the shorter tail
                                     was offset by the longer last epilogue), 1 = on, k in 2..15 =
                                     every tile in k parts (tests).  Results are bit-identical     */
+    GBMI_OPT_TAIL_COLS = 14      /* tensor-core launches of one dataset or cross pair: the tiles of
+                                    the last partial wave (tiles mod concurrent tile slots) run as
+                                    2 to 4 column shares each, every share an MMA as wide as its
+                                    columns over all samples (no combining step), the count chosen
+                                    so the shares fill the fewest share-length waves: 1 = automatic
+                                    (default), 0 = off, k in 2..4 = every tile in k shares (tests).
+                                    Ignored while GBMI_OPT_TAIL_SPLIT is on.  Results are
+                                    bit-identical                                                */
 } gbmi_option;
 
 /* ---------------------------------------------------------------- core calls */

@@ -105,6 +105,7 @@ gbmi_status tile_list(DeviceCtx& c, int64_t n_a, int64_t n_b, bool sym, int bn, 
         c.tl_group = group;
         c.tl_bn = bn;
         c.tl_bm = bm;
+        ++c.tl_gen;
     }
     *count = static_cast<int>(c.tl_host.size());
     return GBMI_OK;
@@ -136,9 +137,7 @@ int tail_split_plan(int tiles, int units, int64_t k_blocks, int* parts) {
 gbmi_status tail_split_list(DeviceCtx& c, int S, int parts, int* count) {
     const int T = static_cast<int>(c.tl_host.size());
     const int n = T - S + S * parts;
-    if (!(c.ts_key_tiles == T && c.ts_key_s == S && c.ts_key_p == parts &&
-          c.ts_key_na == c.tl_na && c.ts_key_nb == c.tl_nb && c.ts_key_bn == c.tl_bn &&
-          c.ts_key_bm == c.tl_bm && c.ts_key_group == c.tl_group)) {
+    if (!(c.ts_key_gen == c.tl_gen && c.ts_key_s == S && c.ts_key_p == parts)) {
         c.ts_host.assign(c.tl_host.begin(), c.tl_host.begin() + (T - S));
         for (int s = 0; s < S; ++s)
             for (int p = 0; p < parts; ++p) {
@@ -151,14 +150,9 @@ gbmi_status tail_split_list(DeviceCtx& c, int S, int parts, int* count) {
                                   c.ts_host.size() * sizeof(GramTile), cudaMemcpyHostToDevice,
                                   g_stream),
                   "split tile list upload");
-        c.ts_key_tiles = T;
+        c.ts_key_gen = c.tl_gen;
         c.ts_key_s = S;
         c.ts_key_p = parts;
-        c.ts_key_na = c.tl_na;
-        c.ts_key_nb = c.tl_nb;
-        c.ts_key_bn = c.tl_bn;
-        c.ts_key_bm = c.tl_bm;
-        c.ts_key_group = c.tl_group;
     }
     GBMI_TRY(ensure(c.part_counts,
                     static_cast<size_t>(S) * (parts - 1) * gram_part_slot_ints() * sizeof(int32_t),
@@ -167,6 +161,71 @@ gbmi_status tail_split_list(DeviceCtx& c, int S, int parts, int* count) {
                     static_cast<size_t>(S) * gram_part_slot_counters() * sizeof(unsigned int),
                     "split tile counters"));
     *count = n;
+    return GBMI_OK;
+}
+
+// Column shares of the tail (GBMI_OPT_TAIL_COLS): a persistent launch of T
+// whole tiles on U concurrent tile slots ends with a partial wave of r = T mod
+// U tiles while the other slots idle.  Those r tiles instead run as `parts`
+// column shares each, every share an MMA as wide as its columns over all
+// samples, so no share waits for another; parts (2..4) is the count whose
+// shares fill the fewest part-length waves, ceil(parts r / U) / parts, the
+// smallest first on ties (wider MMAs).  1 = automatic, k in 2..4 = every tile
+// in k shares (tests), 0 = off.  Returns the number of tiles at the end of the
+// list to split (0: none).
+int tail_cols_plan(int tiles, int units, int* parts) {
+    *parts = 0;
+    if (g_opt.tail_cols == 0 || tiles <= 0 || units <= 0) return 0;
+    if (g_opt.tail_cols >= 2) {
+        *parts = g_opt.tail_cols;
+        return tiles;
+    }
+    const int r = tiles % units;
+    if (tiles < units || r == 0) return 0;
+    int best = 0;
+    double best_len = 1.0;   // a share plan must end before one whole-tile wave
+    for (int p = 2; p <= 4; ++p) {
+        const double len = static_cast<double>((p * r + units - 1) / units) / p;
+        if (len < best_len - 1e-9) {
+            best_len = len;
+            best = p;
+        }
+    }
+    if (best == 0) return 0;
+    *parts = best;
+    return r;
+}
+
+// The cached list c.tl_host with each of its last S tiles as `parts` column
+// shares (tiles whose column window is narrower than 32 * parts stay whole),
+// uploaded to c.col_tiles.
+gbmi_status tail_cols_list(DeviceCtx& c, int S, int parts, int64_t n_b, bool sym, int bn,
+                           int bm, int* count) {
+    const int T = static_cast<int>(c.tl_host.size());
+    if (!(c.tc_key_gen == c.tl_gen && c.tc_key_s == S && c.tc_key_p == parts)) {
+        c.tc_host.assign(c.tl_host.begin(), c.tl_host.begin() + (T - S));
+        for (int s = T - S; s < T; ++s) {
+            GramTile g = c.tl_host[static_cast<size_t>(s)];
+            const ColWindow w = gram_tile_window(n_b, sym, bn, g, bm, false);
+            if (w.hi - w.lo < 32 * parts) {
+                c.tc_host.push_back(g);
+                continue;
+            }
+            for (int p = 0; p < parts; ++p) {
+                g.split = gram_cols_code(p, parts);
+                c.tc_host.push_back(g);
+            }
+        }
+        GBMI_TRY(ensure(c.col_tiles, c.tc_host.size() * sizeof(GramTile), "column-share tiles"));
+        GBMI_CUDA(cudaMemcpyAsync(c.col_tiles.p, c.tc_host.data(),
+                                  c.tc_host.size() * sizeof(GramTile), cudaMemcpyHostToDevice,
+                                  g_stream),
+                  "column-share tile upload");
+        c.tc_key_gen = c.tl_gen;
+        c.tc_key_s = S;
+        c.tc_key_p = parts;
+    }
+    *count = static_cast<int>(c.tc_host.size());
     return GBMI_OK;
 }
 
@@ -397,6 +456,24 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
             L.part_arrive = static_cast<unsigned int*>(c.part_arrive.p);
         }
     }
+    // Otherwise every launch may run the tail's tiles as column shares.
+    const GramTile* all_tiles = plain_tiles;
+    int all_num = plain_num;
+    if (split_slots == 0 && num_shards == 1 && dmaps == nullptr) {
+        const int units = pair ? static_cast<int>(std::min<int64_t>(c.pair_clusters, tiles))
+                               : grid;
+        int parts = 0;
+        const int S = tail_cols_plan(tiles, units, &parts);
+        if (S > 0) {
+            GBMI_TRY(tail_cols_list(c, S, parts, proto.n_b, proto.symmetric != 0, bn, bm,
+                                    &all_num));
+            all_tiles = static_cast<const GramTile*>(c.col_tiles.p);
+            mi_tiles = all_tiles;
+            mi_num = all_num;
+        }
+    }
+    const int all_grid = pair ? 2 * static_cast<int>(std::min<int64_t>(c.pair_clusters, all_num))
+                              : rt::grid_for(c, all_num);
     for (int64_t k0 = 0; k0 < kb_total; k0 += kb_chunk) {
         L.job0.k_begin = static_cast<int32_t>(k0);
         L.job0.k_blocks = static_cast<int32_t>(std::min(kb_chunk, kb_total - k0));
@@ -409,8 +486,8 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
             L.mode = k0 == 0 ? kTcModeCounts : kTcModeCountsAdd;
         }
         const bool split = L.mode == kTcModeMI && split_slots > 0;
-        L.tiles = split ? mi_tiles : plain_tiles;
-        L.num_tiles = split ? mi_num : plain_num;
+        L.tiles = split ? mi_tiles : all_tiles;
+        L.num_tiles = split ? mi_num : all_num;
         if (split)
             GBMI_CUDA(cudaMemsetAsync(L.part_arrive, 0,
                                       static_cast<size_t>(split_slots) *
@@ -418,7 +495,7 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
                                       g_stream),
                       "split tile counters");
         GBMI_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned int), g_stream), "tile counter");
-        GBMI_LAUNCH(launch_gram_tc(maps, L, split ? mi_grid : grid, g_stream),
+        GBMI_LAUNCH(launch_gram_tc(maps, L, split ? mi_grid : all_grid, g_stream),
                     L.mode == kTcModeMI ? "gram_tc_fused_mi" : "gram_tc_counts");
     }
     return GBMI_OK;
@@ -1371,6 +1448,10 @@ gbmi_status gbmi_set_option(int option, int64_t value) {
             if (value < 0 || value > 15) return fail(GBMI_ERR_ARG, "tail split must be in [0, 15]");
             g_opt.tail_split = static_cast<int>(value);
             return GBMI_OK;
+        case GBMI_OPT_TAIL_COLS:
+            if (value < 0 || value > 4) return fail(GBMI_ERR_ARG, "tail columns must be in [0, 4]");
+            g_opt.tail_cols = static_cast<int>(value);
+            return GBMI_OK;
         case GBMI_OPT_CSR_PATH:
             if (value < 0 || value > 2) return fail(GBMI_ERR_ARG, "CSR path must be 0, 1 or 2");
             g_opt.csr_path = static_cast<int>(value);
@@ -1453,6 +1534,7 @@ gbmi_status gbmi_shutdown(void) {
         rt::release(c->split_tiles);
         rt::release(c->split_part);
         rt::release(c->tail_tiles);
+        rt::release(c->col_tiles);
         rt::release(c->part_counts);
         rt::release(c->part_arrive);
         rt::release(c->peak_err);

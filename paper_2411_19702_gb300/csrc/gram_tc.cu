@@ -192,33 +192,17 @@ __device__ __forceinline__ const GramJob& job_of(const GramLaunch& L, int j) {
     return L.jobs != nullptr ? L.jobs[j] : L.job0;
 }
 
-// MMA width of a tile: the job's tile width, or, for the ragged last column
-// block, its valid columns rounded up to 32 (a valid N for M = 128 on one CTA
-// and M = 256 on a pair), at most the tile width (240 = 15 x 16 is valid for
-// both); the columns beyond are masked by every epilogue.
-__device__ __forceinline__ int tile_n(const GramJob& job, const GramTile& tile) {
-    const int64_t w = static_cast<int64_t>(job.n_b) - static_cast<int64_t>(tile.J) * job.bn;
-    if (w >= job.bn) return job.bn;
-    const int n = static_cast<int>((w + 31) / 32 * 32);
-    return n < 32 ? 32 : (n > job.bn ? job.bn : n);
-}
-
-// Columns [0, c0) of a tile of a symmetric job lie below the diagonal for all
-// of its rows (tile rows start at tile_m I, its columns at bn J): its MMAs and
-// B copies start at column c0, a multiple of 32, and accumulator column a holds
-// tile column c0 + a.  0 for cross jobs and direct operands.
-__device__ __forceinline__ int tile_c0(const GramJob& job, const GramTile& tile, int tile_m,
-                                       bool direct) {
-    if (job.symmetric == 0 || direct) return 0;
-    const int64_t skip = static_cast<int64_t>(tile.I) * tile_m - static_cast<int64_t>(tile.J) * job.bn;
-    return skip > 0 ? static_cast<int>(skip & ~int64_t{31}) : 0;
+// Column window [lo, hi) of a tile that its MMAs compute (gram_tile_window).
+__device__ __forceinline__ ColWindow tile_window(const GramJob& job, const GramTile& tile,
+                                                 int tile_m, bool direct) {
+    return gram_tile_window(job.n_b, job.symmetric != 0, job.bn, tile, tile_m, direct);
 }
 
 // K blocks [kb0, kb1) of the job that a tile accumulates: all of them, or its
 // part's share for a split tile.
 __device__ __forceinline__ void tile_krange(const GramJob& job, const GramTile& tile, int& kb0,
                                             int& kb1) {
-    if (tile.split == 0) {
+    if (!split_is_k(tile.split)) {
         kb0 = 0;
         kb1 = job.k_blocks;
         return;
@@ -291,14 +275,14 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
                                                                                : &maps.box64);
         // pair: the partner CTA holds B rows [N/2, N) of the tile's MMA width N;
         // each CTA's half is one box of 120 rows when N = 240, else of 128
-        const int c0 = tile_c0(job, tile, Plan<kPair>::tile_m, L.direct != 0);
-        const int nhalf = kPair ? (tile_n(job, tile) - c0) / 2 : 0;
+        const ColWindow win = tile_window(job, tile, Plan<kPair>::tile_m, L.direct != 0);
+        const int nhalf = kPair ? (win.hi - win.lo) / 2 : 0;
         const bool half120 = kPair && nhalf == 120;
         const CUtensorMap* mapH = half120 ? &maps.box120 : &maps.box128;
         const uint32_t bytes = static_cast<uint32_t>(
             (Plan<kPair>::tile_m + (kPair ? (half120 ? 240 : 2 * kTcBM) : brows)) * kTcBK);
         const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m;
-        const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn + c0;
+        const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn + win.lo;
         if (L.direct && ((a0 | b0) & 15) != 0) {
             // a direct copy's x coordinate (a variable index) must be a multiple
             // of 16 bytes: record it and issue nothing
@@ -368,6 +352,28 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
 }
 
 // ------------------------------------------------------------------ MMA issuer
+// The MMAs of one K block of K-major operands (128 bytes of K: four MMAs of 32
+// bytes, stepping the descriptors' start address inside the swizzled rows);
+// acc0 = 0 starts the accumulator over with the first.
+template <bool kPair, bool kFp4>
+__device__ __forceinline__ void mma_kblock(uint32_t d, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                           uint32_t acc0) {
+#pragma unroll
+    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
+        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
+        const uint32_t accumulate = kk == 0 ? acc0 : 1u;
+        if constexpr (kPair && kFp4)
+            ptx::mma_mxf4_pair(d, adesc + off, bdesc + off, idesc, sfa, sfb, accumulate);
+        else if constexpr (kPair)
+            ptx::mma_f8f6f4_pair(d, adesc + off, bdesc + off, idesc, accumulate);
+        else if constexpr (kFp4)
+            ptx::mma_mxf4(d, adesc + off, bdesc + off, idesc, sfa, sfb, accumulate);
+        else
+            ptx::mma_f8f6f4(d, adesc + off, bdesc + off, idesc, accumulate);
+    }
+}
+
 // kFp4: the launch's operands are the FP4 form (block-scaled MMA); one copy of
 // the issue loop per form, so the per-K-block loop carries no branch on it.
 template <bool kPair, bool kFp4>
@@ -380,6 +386,19 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
     int qslot = 0;
     uint32_t qphase = 0;
     bool ok = true;
+    // Stage s's barriers and operand descriptors are stage 0's plus s times a
+    // constant (barriers 8 bytes apart; descriptors count 16-byte units in
+    // their 14-bit start-address field, which no stage of the 227 KB shared
+    // memory overflows).
+    const uint32_t full0 = sm.full(0), empty0 = sm.empty(0);
+    constexpr uint32_t kStageDesc = static_cast<uint32_t>(Plan<kPair>::stage_bytes >> 4);
+    const bool mn_major = !kFp4 && !kPair && L.direct;
+    const uint64_t adesc0 =
+        mn_major ? ptx::smem_desc_mnmajor_sw128(ptx::smem_u32(sm.a(0)), kTcBM * kTcBK)
+                 : ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(0)));
+    const uint64_t bdesc0 =
+        mn_major ? ptx::smem_desc_mnmajor_sw128(ptx::smem_u32(sm.b(0)), kTcBM * kTcBK)
+                 : ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(0)));
     while (ok) {
         if (!ptx::mbar_wait_bounded(sm.qfull(qslot), qphase, L.timeout_ns, sm.abort_flag())) {
             raise_abort(sm, L.err, kErrTimeoutMma);
@@ -394,8 +413,8 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
         if (t < 0) break;
         const GramTile tile = L.tiles[t];
         const GramJob& job = job_of(L, tile.job);
-        const uint32_t mma_n = static_cast<uint32_t>(
-            tile_n(job, tile) - tile_c0(job, tile, Plan<kPair>::tile_m, L.direct != 0));
+        const ColWindow win = tile_window(job, tile, Plan<kPair>::tile_m, L.direct != 0);
+        const uint32_t mma_n = static_cast<uint32_t>(win.hi - win.lo);
         const uint32_t idesc =
             kFp4 ? ptx::idesc_mxf4_f32(kPair ? 2 * kTcBM : kTcBM, mma_n)
             : kPair ? ptx::idesc_e4m3_f32(2 * kTcBM, mma_n)
@@ -412,73 +431,53 @@ __device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tme
         }
         ptx::tc_fence_after();
         const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kAccCols);
-        for (int kb = 0; kb < k_blocks; ++kb) {
-            if (!ptx::mbar_wait_bounded(sm.full(stage), phase, L.timeout_ns, sm.abort_flag())) {
-                raise_abort(sm, L.err, kErrTimeoutMma);
-                ok = false;
-                break;
-            }
+        // One K block: wait for its stage, issue its MMAs, release the stage
+        // when they complete.  The tensor pipe queues few MMAs, so the cycles
+        // this thread spends between K blocks show up as idle tensor time: the
+        // loop below runs two K blocks per iteration with the addresses above
+        // (measured with the copies and the epilogue switched off: 560 -> 483
+        // SM cycles per K block of a 256 x 240 FP4 tile, the MMAs' own rate).
+        auto kblock = [&](int kb) -> bool {
+            const uint32_t st = static_cast<uint32_t>(stage);
+            const uint32_t fb = full0 + 8u * st;
+            if (!ptx::mbar_try_wait(fb, phase) &&
+                !ptx::mbar_wait_bounded(fb, phase, L.timeout_ns, sm.abort_flag()))
+                return false;
             ptx::tc_fence_after();
-            if constexpr (kPair) {
-                const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
-                const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
-                if constexpr (kFp4) {
-#pragma unroll
-                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
-                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
-                        ptx::mma_mxf4_pair(d_tmem, adesc + off, bdesc + off, idesc, sfa, sfb,
-                                           (kb | kk) != 0 ? 1u : 0u);
-                    }
-                } else {
-#pragma unroll
-                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
-                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
-                        ptx::mma_f8f6f4_pair(d_tmem, adesc + off, bdesc + off, idesc,
-                                             (kb | kk) != 0 ? 1u : 0u);
-                    }
-                }
-            } else if (!kFp4 && L.direct) {
+            const uint64_t adesc = adesc0 + kStageDesc * st;
+            const uint64_t bdesc = bdesc0 + kStageDesc * st;
+            const uint32_t acc0 = kb != 0 ? 1u : 0u;
+            if (mn_major) {
                 // MN-major: 128-sample K-rows of 128 bytes, 128-variable atoms of
                 // B 16 KB apart; K step kk starts kk * 32 rows (4 atoms) further
-                const uint64_t adesc =
-                    ptx::smem_desc_mnmajor_sw128(ptx::smem_u32(sm.a(stage)), kTcBM * kTcBK);
-                const uint64_t bdesc =
-                    ptx::smem_desc_mnmajor_sw128(ptx::smem_u32(sm.b(stage)), kTcBM * kTcBK);
 #pragma unroll
                 for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
                     const uint64_t off = static_cast<uint64_t>((kk * kUmmaK * kTcBK) >> 4);
                     ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
-                                    (kb | kk) != 0 ? 1u : 0u);
+                                    kk == 0 ? acc0 : 1u);
                 }
             } else {
-                const uint64_t adesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.a(stage)));
-                const uint64_t bdesc = ptx::smem_desc_kmajor_sw128(ptx::smem_u32(sm.b(stage)));
-                if constexpr (kFp4) {
-#pragma unroll
-                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
-                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
-                        ptx::mma_mxf4(d_tmem, adesc + off, bdesc + off, idesc, sfa, sfb,
-                                      (kb | kk) != 0 ? 1u : 0u);
-                    }
-                } else {
-#pragma unroll
-                    for (int kk = 0; kk < kTcBK / kUmmaK; ++kk) {
-                        // advance the start address by kk * 32 bytes inside the swizzle row
-                        const uint64_t off = static_cast<uint64_t>((kk * kUmmaK) >> 4);
-                        ptx::mma_f8f6f4(d_tmem, adesc + off, bdesc + off, idesc,
-                                        (kb | kk) != 0 ? 1u : 0u);
-                    }
-                }
+                mma_kblock<kPair, kFp4>(d_tmem, adesc, bdesc, idesc, sfa, sfb, acc0);
             }
             if constexpr (kPair)
-                ptx::mma_commit_pair(sm.empty(stage));
+                ptx::mma_commit_pair(empty0 + 8u * st);
             else
-                ptx::mma_commit(sm.empty(stage));   // frees the slot when these MMAs finish
+                ptx::mma_commit(empty0 + 8u * st);   // frees the slot when these MMAs finish
             if (++stage == kStages) {
                 stage = 0;
                 phase ^= 1u;
             }
+            return true;
+        };
+        int kb = 0;
+        for (; kb + 1 < k_blocks; kb += 2) {
+            if (!kblock(kb) || !kblock(kb + 1)) {
+                ok = false;
+                break;
+            }
         }
+        if (ok && kb < k_blocks && !kblock(kb)) ok = false;
+        if (!ok) raise_abort(sm, L.err, kErrTimeoutMma);
         if (!ok) break;
         if constexpr (kPair)                    // both CTAs' halves are ready
             ptx::mma_commit_pair_multicast(sm.tfull(acc), static_cast<uint16_t>(3u));
@@ -564,10 +563,12 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
         // copies in registers: the epilogue's stores could otherwise alias the
         // job table and force these fields to be reloaded after every store
         const MiParams P = job.mp;
-        // columns of this warp: a multiple of 16 (240-wide tiles: 64, 64, 64, 48)
-        const int per = ((job.bn + nparts - 1) / nparts + 15) & ~15;
-        const int col_base = part * per;
-        const int cols = max(0, min(per, job.bn - col_base));
+        // columns of this warp: an equal share of the unit's column window, a
+        // multiple of 16 (a whole 240-wide tile on three warps: 80 each)
+        const ColWindow win = tile_window(job, tile, Plan<kPair>::tile_m, L.direct != 0);
+        const int per = ((win.hi - win.lo + nparts - 1) / nparts + 15) & ~15;
+        const int col_base = win.lo + part * per;
+        const int cols = max(0, min(per, win.hi - col_base));
         const int64_t n_a = job.n_a, n_b = job.n_b;
         const bool sym = job.symmetric != 0;
         const int64_t ibase = static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m +
@@ -597,11 +598,9 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             break;
         }
         ptx::tc_fence_after();
-        // accumulator column of tile column col_base + c: col_base + c - c0 (the
-        // epilogue reads no column below c0: those lie below the diagonal)
-        const int c0 = tile_c0(job, tile, Plan<kPair>::tile_m, L.direct != 0);
+        // accumulator column of tile column col_base + c: col_base + c - win.lo
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(lane_base) << 16) +
-                               static_cast<uint32_t>(acc * kAccCols + col_base - c0);
+                               static_cast<uint32_t>(acc * kAccCols + col_base - win.lo);
         if constexpr (is_mi<kMode>()) {
             // MI: chunks of 4 columns in one small loop body; the next chunk's
             // accumulator columns load from TMEM during this chunk's math.
@@ -626,7 +625,7 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             // 2^24 samples) and evaluates MI as for a whole tile.  The wait
             // ends: the units it waits for are earlier in the tile list, so
             // none of them waits on it.
-            if (tile.split != 0) {
+            if (split_is_k(tile.split)) {
                 const int parts = tile.split & 15, part = (tile.split >> 4) & 15;
                 const int64_t slot = (tile.split >> 8) - 1;
                 const int64_t wbase = (static_cast<int64_t>(sm.rank) * kNepi + (warp - 2)) *

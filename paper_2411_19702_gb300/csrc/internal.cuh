@@ -176,19 +176,77 @@ struct GramJob {
 };
 
 // One 128 x bn output tile: job index, row block I, column block J.
-// split = 0: the whole tile.  Otherwise the tile is one of `parts` units that
-// each accumulate a contiguous share of the job's K blocks:
-//   split = ((slot + 1) << 8) | (part << 4) | parts   (2 <= parts <= 15)
-// Units 0 .. parts-2 store their exact int32 counts in the slot's part of
-// GramLaunch.part_counts and count themselves in on the slot's counters; unit
-// parts-1, listed after them, waits for them, adds their counts to its own and
-// runs the MI epilogue (the tail of a launch finishes in pieces of 1 / parts
-// of a tile, so fewer SMs idle).
+// split = 0: the whole tile.  Otherwise either
+// - a K share (bit 30 clear): the tile is one of `parts` units that each
+//   accumulate a contiguous share of the job's K blocks:
+//     split = ((slot + 1) << 8) | (part << 4) | parts   (2 <= parts <= 15)
+//   Units 0 .. parts-2 store their exact int32 counts in the slot's part of
+//   GramLaunch.part_counts and count themselves in on the slot's counters; unit
+//   parts-1, listed after them, waits for them, adds their counts to its own
+//   and runs the MI epilogue;
+// - a column share (bit 30 set): split = kSplitCols | (part << 4) | parts; the
+//   unit computes part `part` of `parts` of the tile's column window (below)
+//   over all K blocks, with an MMA as wide as its share and no combining step.
+// Either way the tail of a launch finishes in pieces of a tile, so fewer SMs
+// idle.
 struct GramTile {
     int32_t job, I, J, split;
 };
+constexpr int32_t kSplitCols = 1 << 30;
 __host__ __device__ inline int32_t gram_split_code(int slot, int part, int parts) {
     return ((slot + 1) << 8) | (part << 4) | parts;
+}
+__host__ __device__ inline int32_t gram_cols_code(int part, int parts) {
+    return kSplitCols | (part << 4) | parts;
+}
+__host__ __device__ inline bool split_is_k(int32_t split) {
+    return split != 0 && (split & kSplitCols) == 0;
+}
+
+// MMA width of a tile: the job's tile width bn, or, for the ragged last column
+// block, its valid columns rounded up to 32 (a valid N for M = 128 on one CTA
+// and M = 256 on a pair), at most bn (240 = 15 x 16 is valid for both); the
+// columns beyond are masked by every epilogue.
+__host__ __device__ inline int gram_tile_n(int64_t n_b, int bn, int J) {
+    const int64_t w = n_b - static_cast<int64_t>(J) * bn;
+    if (w >= bn) return bn;
+    const int n = static_cast<int>((w + 31) / 32 * 32);
+    return n < 32 ? 32 : (n > bn ? bn : n);
+}
+// Columns [0, c0) of a tile of a symmetric job lie below the diagonal for all
+// of its rows (tile rows start at tile_m I, its columns at bn J): its MMAs and
+// B copies start at column c0, a multiple of 32.  0 for cross jobs and direct
+// operands.
+__host__ __device__ inline int gram_tile_c0(bool symmetric, int bn, int I, int J, int tile_m,
+                                            bool direct) {
+    if (!symmetric || direct) return 0;
+    const int64_t skip = static_cast<int64_t>(I) * tile_m - static_cast<int64_t>(J) * bn;
+    return skip > 0 ? static_cast<int>(skip & ~int64_t{31}) : 0;
+}
+// Column window [lo, hi) of the tile that a unit's MMAs compute: [c0, n) with
+// n = gram_tile_n for a whole tile (or a K share); for a column share, piece
+// `part` of `parts` of it, cut at multiples of 32 after c0.  Every piece is a
+// non-empty multiple of 16 wide when hi - lo of the whole window is at least
+// 32 * parts (the host splits no narrower tile).  Accumulator column a holds
+// tile column lo + a.
+struct ColWindow {
+    int lo, hi;
+};
+__host__ __device__ inline ColWindow gram_tile_window(int64_t n_b, bool symmetric, int bn,
+                                                      const GramTile& t, int tile_m,
+                                                      bool direct) {
+    const int c0 = gram_tile_c0(symmetric, bn, t.I, t.J, tile_m, direct);
+    const int n = gram_tile_n(n_b, bn, t.J);
+    ColWindow w{c0, n};
+    if ((t.split & kSplitCols) != 0) {
+        const int parts = t.split & 15, part = (t.split >> 4) & 15;
+        const int width = n - c0;
+        const int lo = part == 0 ? 0 : ((width * part / parts + 16) & ~31);
+        const int hi = part + 1 == parts ? width : ((width * (part + 1) / parts + 16) & ~31);
+        w.lo = c0 + lo;
+        w.hi = c0 + hi;
+    }
+    return w;
 }
 
 struct GramLaunch {

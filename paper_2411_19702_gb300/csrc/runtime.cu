@@ -60,6 +60,7 @@ struct EnvOptions {
         if (num("GBMI_GROUP_COLS", 1, 1 << 20, &v)) g_opt.group_cols = static_cast<int>(v);
         if (num("GBMI_MAX_CTAS", 0, 1 << 20, &v)) g_opt.max_ctas = static_cast<int>(v);
         if (num("GBMI_TAIL_SPLIT", 0, 15, &v)) g_opt.tail_split = static_cast<int>(v);
+        if (num("GBMI_TAIL_COLS", 0, 4, &v)) g_opt.tail_cols = static_cast<int>(v);
     }
 };
 EnvOptions g_env_options;

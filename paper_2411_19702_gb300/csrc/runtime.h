@@ -36,6 +36,7 @@ struct Options {
     int split_k = 0;                     // sample split of few-tile Grams: 0 auto, 1 off, 2 forced
     int fp4 = 1;                         // tensor-core operands in the FP4 form (block-scaled MMA)
     int tail_split = 0;                  // fused MI launch: last tiles in K-share units (off)
+    int tail_cols = 1;                   // last partial wave in column shares (automatic)
 };
 
 struct DeviceCtx {
@@ -63,13 +64,18 @@ struct DeviceCtx {
     unsigned int* dflags = nullptr;   // its device address
     int hflags_cap = 0;
     std::vector<GramTile> tl_host;
+    int64_t tl_gen = 0;   // bumped whenever tl_host is rebuilt
     // split tile list of the fused MI launch (the cached list with its last
-    // tiles as K-share units), keyed by the cached list and the split
+    // tiles as K-share units), keyed by the cached list's generation and the split
     DevBuf tail_tiles, part_counts, part_arrive;
     std::vector<GramTile> ts_host;
-    int ts_key_tiles = -1, ts_key_s = -1, ts_key_p = -1, ts_key_bn = -1, ts_key_bm = -1,
-        ts_key_group = -1;
-    int64_t ts_key_na = -1, ts_key_nb = -1;
+    int64_t ts_key_gen = -1;
+    int ts_key_s = -1, ts_key_p = -1;
+    // the cached list with its last tiles as column shares, keyed likewise
+    DevBuf col_tiles;
+    std::vector<GramTile> tc_host;
+    int64_t tc_key_gen = -1;
+    int tc_key_s = -1, tc_key_p = -1;
 };
 
 extern std::recursive_mutex g_mu;

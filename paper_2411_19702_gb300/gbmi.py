@@ -21,7 +21,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_BINARY, ERR_UNSUPPORTED = r
 PATH_AUTO, PATH_FUSED, PATH_PLAIN, PATH_POPCOUNT = range(4)
 (OPT_FIXUP, OPT_TIMEOUT_NS, OPT_DEBUG_FLAGS, OPT_GROUP_COLS, OPT_MAX_CTAS, OPT_PROFILE,
  OPT_TILE_N, OPT_DIRECT, OPT_PAIR, OPT_CSR_PATH, OPT_SPLIT_K, OPT_FP4,
- OPT_TAIL_SPLIT) = range(1, 14)
+ OPT_TAIL_SPLIT, OPT_TAIL_COLS) = range(1, 15)
 _PATHS = {"auto": PATH_AUTO, "fused": PATH_FUSED, "plain": PATH_PLAIN, "popcount": PATH_POPCOUNT}
 STATUS_NAMES = {OK: "OK", ERR_ARG: "ERR_ARG", ERR_OOM: "ERR_OOM", ERR_CUDA: "ERR_CUDA",
                 ERR_TIMEOUT: "ERR_TIMEOUT", ERR_NOT_BINARY: "ERR_NOT_BINARY",

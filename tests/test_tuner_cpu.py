@@ -44,6 +44,16 @@ def test_tuner_rejects_bad_widths():
         gbmi.set_option(gbmi.OPT_TILE_N, 100)
 
 
+def test_tail_options_range():
+    for bad in (5, -1):
+        with pytest.raises(gbmi.GbmiError):
+            gbmi.set_option(gbmi.OPT_TAIL_COLS, bad)
+    with pytest.raises(gbmi.GbmiError):
+        gbmi.set_option(gbmi.OPT_TAIL_SPLIT, 16)
+    for ok in (0, 2, 3, 4, 1):
+        gbmi.set_option(gbmi.OPT_TAIL_COLS, ok)
+
+
 def test_autotune_table_round_trip(tmp_path):
     table = {"16,26": {"m": 100_000, "n": 10_000, "tile_n": 128, "pair": 1,
                        "ms": {"single64": 3.0, "single128": 2.0, "single256": 2.5,
