@@ -230,9 +230,13 @@ template <bool kPair>
 __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
                              const GramLaunch& L) {
     constexpr int kStages = Plan<kPair>::stages;
-    int pending_parity[kStages];
-#pragma unroll
-    for (int s = 0; s < kStages; ++s) pending_parity[s] = -1;
+    // stages with a copy issued (bit s), and the barrier phase parity it
+    // completes (bit s): registers, where an array indexed by the run-time
+    // stage would live in local memory
+    uint32_t issued = 0, issued_par = 0;
+    const uint32_t full0 = sm.full(0), empty0 = sm.empty(0);
+    const uint32_t a_smem0 = ptx::smem_u32(sm.a(0)), b_smem0 = ptx::smem_u32(sm.b(0));
+    constexpr uint32_t kStageBytes = static_cast<uint32_t>(Plan<kPair>::stage_bytes);
     int stage = 0;
     uint32_t phase = 0;
     int qslot = 0;
@@ -292,6 +296,64 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         }
         int kb_lo = 0, kb_hi = 0;
         tile_krange(job, tile, kb_lo, kb_hi);
+        if (kPair || !L.direct) {
+            // One K block of packed operands: wait for a free stage, then load
+            // A and B (a pair's CTA 0 loads both CTAs' halves, rows +0 and +128
+            // of A and +0 and +N/2 of B, every copy completing on CTA 0's full
+            // barrier).  Stage s's addresses are stage 0's plus s stages, the
+            // row coordinates advance by the operand strides, and the loop runs
+            // two K blocks per iteration, so that a freed stage is refilled with
+            // little delay.
+            const int64_t k0 = static_cast<int64_t>(job.k_begin) + kb_lo;
+            int32_t ya = static_cast<int32_t>(a0 + k0 * job.strideA);
+            int32_t yb = static_cast<int32_t>(b0 + k0 * job.strideB);
+            const int32_t dya = static_cast<int32_t>(job.strideA);
+            const int32_t dyb = static_cast<int32_t>(job.strideB);
+            auto load = [&]() -> bool {
+                const uint32_t st = static_cast<uint32_t>(stage);
+                const uint32_t eb = empty0 + 8u * st, fb = full0 + 8u * st;
+                if (!ptx::mbar_try_wait(eb, phase ^ 1u) &&
+                    !ptx::mbar_wait_bounded(eb, phase ^ 1u, L.timeout_ns, sm.abort_flag()))
+                    return false;
+                ptx::mbar_arrive_expect_tx(fb, bytes);
+                const uint32_t a_s = a_smem0 + kStageBytes * st;
+                const uint32_t b_s = b_smem0 + kStageBytes * st;
+                ptx::tma_load_2d(a_s, &maps.box128, fb, 0, ya);
+                if constexpr (kPair) {
+                    ptx::tma_load_2d(b_s, mapH, fb, 0, yb);
+                    ptx::tma_load_2d_peer(ptx::mapa_shared(a_s, 1u), &maps.box128, fb, 0,
+                                          ya + kTcBM);
+                    ptx::tma_load_2d_peer(ptx::mapa_shared(b_s, 1u), mapH, fb, 0, yb + nhalf);
+                } else {
+                    ptx::tma_load_2d(b_s, mapB, fb, 0, yb);
+                }
+                issued |= 1u << st;
+                issued_par = (issued_par & ~(1u << st)) | (phase << st);
+                ya += dya;
+                yb += dyb;
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+                return true;
+            };
+            int kb = kb_lo;
+            for (; kb + 1 < kb_hi; kb += 2) {
+                if (!load() || !load()) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (ok && kb < kb_hi && !load()) ok = false;
+            if (!ok) {
+                raise_abort(sm, L.err, kErrTimeoutLoad);
+                break;
+            }
+            t = t_next;
+            continue;
+        }
+        // direct operands (single CTA): 128 variables x 128 samples of X per
+        // box, B in bn / 128 boxes
         for (int kb = kb_lo; kb < kb_hi; ++kb) {
             if (!ptx::mbar_wait_bounded(sm.empty(stage), phase ^ 1u, L.timeout_ns,
                                         sm.abort_flag())) {
@@ -301,32 +363,14 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
             }
             const int64_t k = job.k_begin + kb;
             ptx::mbar_arrive_expect_tx(sm.full(stage), bytes);
-            if constexpr (kPair) {
-                // CTA 0 loads both CTAs' halves (rows +0 and +128 of A and of B);
-                // every copy completes on CTA 0's full barrier
-                const int32_t ya = static_cast<int32_t>(a0 + k * job.strideA);
-                const int32_t yb = static_cast<int32_t>(b0 + k * job.strideB);
-                ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.box128, sm.full(stage), 0, ya);
-                ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), mapH, sm.full(stage), 0, yb);
-                ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.a(stage)), 1u),
-                                      &maps.box128, sm.full(stage), 0, ya + kTcBM);
-                ptx::tma_load_2d_peer(ptx::mapa_shared(ptx::smem_u32(sm.b(stage)), 1u),
-                                      mapH, sm.full(stage), 0, yb + nhalf);
-            } else if (L.direct) {
-                // 128 variables x 128 samples of X per box; B in bn / 128 boxes
-                const int32_t y = static_cast<int32_t>(k * kTcBK);
-                ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.xa, sm.full(stage),
-                                 static_cast<int32_t>(a0), y);
-                for (int h = 0; h < bn; h += kTcBM)
-                    ptx::tma_load_2d(ptx::smem_u32(sm.b(stage) + h * kTcBK), &maps.xb,
-                                     sm.full(stage), static_cast<int32_t>(b0 + h), y);
-            } else {
-                ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.box128, sm.full(stage), 0,
-                                 static_cast<int32_t>(a0 + k * job.strideA));
-                ptx::tma_load_2d(ptx::smem_u32(sm.b(stage)), mapB, sm.full(stage), 0,
-                                 static_cast<int32_t>(b0 + k * job.strideB));
-            }
-            pending_parity[stage] = static_cast<int>(phase);
+            const int32_t y = static_cast<int32_t>(k * kTcBK);
+            ptx::tma_load_2d(ptx::smem_u32(sm.a(stage)), &maps.xa, sm.full(stage),
+                             static_cast<int32_t>(a0), y);
+            for (int h = 0; h < bn; h += kTcBM)
+                ptx::tma_load_2d(ptx::smem_u32(sm.b(stage) + h * kTcBK), &maps.xb,
+                                 sm.full(stage), static_cast<int32_t>(b0 + h), y);
+            issued |= 1u << stage;
+            issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
             if (++stage == kStages) {
                 stage = 0;
                 phase ^= 1u;
@@ -338,9 +382,9 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         // Unwinding: wait (bounded) until every copy this thread issued has landed.
         const uint64_t d2 = ptx::globaltimer_ns() + 100000000ull;
         for (int s2 = 0; s2 < kStages; ++s2) {
-            if (pending_parity[s2] < 0) continue;
+            if (((issued >> s2) & 1u) == 0) continue;
             const uint32_t bar = sm.full(s2);
-            const uint32_t par = static_cast<uint32_t>(pending_parity[s2]);
+            const uint32_t par = (issued_par >> s2) & 1u;
             while (!ptx::mbar_try_wait(bar, par)) {
                 if (ptx::globaltimer_ns() > d2) {
                     atomicOr(L.err, kErrTimeoutDrain);
