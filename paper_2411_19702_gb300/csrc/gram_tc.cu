@@ -281,10 +281,12 @@ __device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
         // each CTA's half is one box of 120 rows when N = 240, else of 128
         const ColWindow win = tile_window(job, tile, Plan<kPair>::tile_m, L.direct != 0);
         const int nhalf = kPair ? (win.hi - win.lo) / 2 : 0;
-        const bool half120 = kPair && nhalf == 120;
-        const CUtensorMap* mapH = half120 ? &maps.box120 : &maps.box128;
+        // (64 rows when N <= 128: column shares and tiles cut by the diagonal)
+        const int hrows = nhalf == 120 ? 120 : (nhalf <= 64 ? 64 : kTcBM);
+        const CUtensorMap* mapH =
+            hrows == 120 ? &maps.box120 : (hrows == 64 ? &maps.box64 : &maps.box128);
         const uint32_t bytes = static_cast<uint32_t>(
-            (Plan<kPair>::tile_m + (kPair ? (half120 ? 240 : 2 * kTcBM) : brows)) * kTcBK);
+            (Plan<kPair>::tile_m + (kPair ? 2 * hrows : brows)) * kTcBK);
         const int64_t a0 = job.rowA + static_cast<int64_t>(tile.I) * Plan<kPair>::tile_m;
         const int64_t b0 = job.rowB + static_cast<int64_t>(tile.J) * bn + win.lo;
         if (L.direct && ((a0 | b0) & 15) != 0) {
