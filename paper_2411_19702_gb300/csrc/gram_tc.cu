@@ -747,6 +747,28 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                 float v[4];
                 int32_t n11s[4];
                 uint32_t need = 0;   // kFix: pairs that go to the FP64 combine
+                // kFix: the table reads of the chunk's pairs are issued before
+                // their FP32 arithmetic, which hides their latency (the reads
+                // are scattered over the table and mostly miss L1); almost every
+                // pair of sparse data needs them
+                double t[4][4];
+                if constexpr (kFix) {
+                    const bool early = P.fixup && P.T != nullptr;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int64_t j = j0 + q;
+                        int32_t n11 = __float2int_rn(__uint_as_float(cur[q]) * cscale);
+                        const bool ld = early && row_ok && j < n_b && (!sym || j >= i);
+                        if (ld && prefix != nullptr) n11 += prefix[i * ld_out + j];
+                        n11s[q] = n11;
+                        const MiCounts cc =
+                            mi_counts(ld ? n11 : 0, ld ? A.v : 0, ld ? cvf[c + q].v : 0, P);
+                        t[q][0] = ld ? __ldg(P.T + cc.n11) : 0.0;
+                        t[q][1] = ld ? __ldg(P.T + cc.n00) : 0.0;
+                        t[q][2] = ld ? __ldg(P.T + cc.n10) : 0.0;
+                        t[q][3] = ld ? __ldg(P.T + cc.n01) : 0.0;
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int64_t j = j0 + q;
@@ -777,9 +799,8 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                     n11s[q] = n11;
                 }
                 if constexpr (kFix) {
-                    if (__any_sync(0xffffffffu, need != 0)) {
-                        // m MI = T[n11] + T[n10] + T[n01] + T[n00] + K_i + K_j
-                        double t[4][4];
+                    if (!(P.fixup && P.T != nullptr) && __any_sync(0xffffffffu, need != 0)) {
+                        // (no table: the terms evaluated here, for the pairs that need them)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const bool on = (need >> q) & 1u;
@@ -790,6 +811,9 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
                             t[q][2] = on ? nlog2n(cc.n10, P) : 0.0;
                             t[q][3] = on ? nlog2n(cc.n01, P) : 0.0;
                         }
+                    }
+                    if (need != 0) {
+                        // m MI = T[n11] + T[n10] + T[n01] + T[n00] + K_i + K_j
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             if ((need >> q) & 1u) {
