@@ -747,12 +747,43 @@ __device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_
             const bool lean_rows = !kFix && prefix == nullptr && out_t == nullptr && !L.direct &&
                                    ibase + 32 <= n_a && (ld_out & 3) == 0 &&
                                    (reinterpret_cast<uintptr_t>(out_f) & 15u) == 0;
+            const bool lean_rows8 = lean_rows && (ld_out & 7) == 0 &&
+                                    (reinterpret_cast<uintptr_t>(out_f) & 31u) == 0;
 #pragma unroll 1
             for (; c < c_end; c += 4) {
                 uint32_t nxt[4];
                 const bool more = c + 4 < c_end;
                 if (more) ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(c + 4), nxt);
                 const int64_t j0 = jstart + c;
+                if (lean_rows8 && (j0 & 7) == 0 && c + 8 <= c_end && j0 + 8 <= n_b &&
+                    (!sym || j0 > ibase + 31)) {
+                    // two chunks at once (the second is in flight in nxt): each
+                    // row's 8 values leave as one 32-byte store
+                    uint32_t nx2[4];
+                    const bool more2 = c + 8 < c_end;
+                    ptx::tmem_wait_ld();
+                    if (more2) ptx::tmem_ld_32x32b_x4(taddr + static_cast<uint32_t>(c + 8), nx2);
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const MiVarF B = cvf[c + q];
+                        const uint32_t w = q < 4 ? cur[q] : nxt[q - 4];
+                        const MiCounts cc = mi_counts(__float2int_rn(__uint_as_float(w)), A.v, B.v, P);
+                        v[q] = fmaxf(mi_fp32(cc, det_to_float(cc.det), A, B, P), 0.f);
+                    }
+                    if (sym) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) out_f[(j0 + q) * ld_out + i] = v[q];
+                    }
+                    ptx::st_global_v8(out_f + i * ld_out + j0, v);
+                    if (more2) {
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) cur[q] = nx2[q];
+                    }
+                    c += 4;   // + 4 by the loop
+                    continue;
+                }
                 if (lean_rows && j0 + 4 <= n_b && (!sym || j0 > ibase + 31)) {
                     float v[4];
 #pragma unroll
