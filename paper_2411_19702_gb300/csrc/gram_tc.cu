@@ -125,12 +125,21 @@ constexpr int kQ = 8;                            // tile-id queue between the ro
 // full, empty, tmem full x2, tmem empty x2, drain, queue full x kQ, queue empty x kQ
 constexpr int kNumBarsFor(int stages) { return 2 * stages + 4 + 1 + 2 * kQ; }
 
-// Shared-memory plan.  Single CTA: 4 stages of A (128 rows) + B (up to 256
-// rows).  CTA pair: 6 stages of this CTA's halves, 128 rows of A and 128 rows
+// Pipeline stages of a kernel: single CTA 4; CTA pairs 6, except the kernel
+// with the FP64 combine, which takes 5: its epilogue waits on reads scattered
+// over the n log2 n table, and the stage it gives up leaves L1 twice the room
+// (measured at 10^5 x 10^4: its Gram 2.41 -> 1.92 ms, while the FP32 epilogue
+// kernel is slower with fewer than 6).
+__host__ __device__ constexpr int stages_for(int mode, bool pair) {
+    return !pair ? 4 : (mode == kTcModeMI ? 5 : 6);
+}
+
+// Shared-memory plan.  Single CTA: kSt stages of A (128 rows) + B (up to 256
+// rows).  CTA pair: kSt stages of this CTA's halves, 128 rows of A and 128 rows
 // of B (the pair's tile is 256 x 256).
-template <bool kPair>
+template <bool kPair, int kSt = stages_for(kTcModeMI32, kPair)>
 struct Plan {
-    static constexpr int stages = kPair ? 6 : 4;
+    static constexpr int stages = kSt;
     static constexpr int b_bytes = kPair ? kTcBM * kTcBK : kTcBNMax * kTcBK;
     static constexpr int stage_bytes = kABytes + b_bytes;
     static constexpr int tile_m = kPair ? 2 * kTcBM : kTcBM;   // rows of A per tile
@@ -144,9 +153,9 @@ struct Plan {
     static_assert(smem_bytes <= 232448, "shared memory budget");
 };
 
-template <bool kPair>
+template <bool kPair, int kSt = stages_for(kTcModeMI32, kPair)>
 struct Smem {
-    using P = Plan<kPair>;
+    using P = Plan<kPair, kSt>;
     uint8_t* base;
     uint32_t rank;   // CTA rank in the pair (0 when single)
     __device__ uint8_t* a(int s) const { return base + s * P::stage_bytes; }
@@ -178,8 +187,8 @@ struct Smem {
     }
 };
 
-template <bool kPair>
-__device__ __forceinline__ void raise_abort(const Smem<kPair>& sm, unsigned int* err,
+template <bool kPair, int kSt>
+__device__ __forceinline__ void raise_abort(const Smem<kPair, kSt>& sm, unsigned int* err,
                                             uint32_t code) {
     atomicOr(err, code);
     *sm.abort_flag() = 1;
@@ -226,10 +235,10 @@ __device__ __forceinline__ int next_tile(const GramLaunch& L, int s) {
         return blockIdx.x + s * gridDim.x;
 }
 
-template <bool kPair>
-__device__ void run_producer(const Smem<kPair>& sm, const OperandMaps& maps,
+template <bool kPair, int kSt>
+__device__ void run_producer(const Smem<kPair, kSt>& sm, const OperandMaps& maps,
                              const GramLaunch& L) {
-    constexpr int kStages = Plan<kPair>::stages;
+    constexpr int kStages = kSt;
     // stages with a copy issued (bit s), and the barrier phase parity it
     // completes (bit s): registers, where an array indexed by the run-time
     // stage would live in local memory
@@ -422,9 +431,9 @@ __device__ __forceinline__ void mma_kblock(uint32_t d, uint64_t adesc, uint64_t 
 
 // kFp4: the launch's operands are the FP4 form (block-scaled MMA); one copy of
 // the issue loop per form, so the per-K-block loop carries no branch on it.
-template <bool kPair, bool kFp4>
-__device__ void run_mma(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tmem_base) {
-    constexpr int kStages = Plan<kPair>::stages;
+template <bool kPair, bool kFp4, int kSt>
+__device__ void run_mma(const Smem<kPair, kSt>& sm, const GramLaunch& L, uint32_t tmem_base) {
+    constexpr int kStages = kSt;
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
@@ -562,7 +571,8 @@ __device__ __forceinline__ void store_one(const GramJob& g, int64_t row, int64_t
 }
 
 template <int kMode, bool kPair>
-__device__ void run_epilogue(const Smem<kPair>& sm, const GramLaunch& L, uint32_t tmem_base) {
+__device__ void run_epilogue(const Smem<kPair, stages_for(kMode, kPair)>& sm, const GramLaunch& L,
+                             uint32_t tmem_base) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int lane_base = (warp & 3) * 32;             // TMEM lanes this warp may access
@@ -1008,11 +1018,11 @@ template <int kMode, bool kPair>
 __global__ void __launch_bounds__(threads_of(kMode), 1)
 gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__ GramLaunch L) {
     extern __shared__ uint8_t smem_raw[];
-    Smem<kPair> sm;
+    constexpr int kStages = stages_for(kMode, kPair);
+    Smem<kPair, kStages> sm;
     sm.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                          ~static_cast<uintptr_t>(1023));
     sm.rank = kPair ? ptx::cluster_ctarank() : 0u;
-    constexpr int kStages = Plan<kPair>::stages;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const bool lead = sm.rank == 0;   // the CTA that loads and issues the MMAs
@@ -1111,7 +1121,8 @@ cudaError_t set_smem_attrs() {
     const int bytes = static_cast<int>(Plan<kPair>::smem_bytes);
     cudaError_t e;
     e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI, kPair>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(Plan<kPair, stages_for(kTcModeMI, kPair)>::smem_bytes));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI32, kPair>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1130,7 +1141,7 @@ cudaError_t launch_pair(const OperandMaps& maps, const GramLaunch& L, int grid,
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
     cfg.blockDim = dim3(threads_of(kMode), 1, 1);
-    cfg.dynamicSmemBytes = Plan<true>::smem_bytes;
+    cfg.dynamicSmemBytes = Plan<true, stages_for(kMode, true)>::smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
