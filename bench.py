@@ -408,11 +408,17 @@ def measure_batch(dev, reps=3, k=512, seed=4):
            "tiles": plan.tiles, "launches_per_run": launches_per_run,
            "autotuned_buckets": len(table), "autotune_s": tune_s,
            "autotune_choices": {k: {"tile_n": v["tile_n"], "pair": v["pair"],
-                                    "ms": {c: round(t, 4) for c, t in v["ms"].items()}}
+                                    "split": v.get("split", 0),
+                                    "ms": {c: round(t, 4) for c, t in v["ms"].items()},
+                                    "ms_split": {c: round(t, 4)
+                                                 for c, t in v.get("ms_split", {}).items()}}
                                 for k, v in table.items()},
+           "autotune_split_buckets": sum(1 for v in table.values() if v.get("split", 0) != 0),
            "autotune_knobs": "per (floor(log2 m), floor(2 log2 n)) bucket: single-CTA tile "
-                             "width 64/128/256 and single-CTA vs CTA-pair kernel; per batch: "
-                             "the kernel assignment (rule / table / all single / all pairs)",
+                             "width 64/128/256, single-CTA vs CTA-pair kernel, and (n <= 3000) "
+                             "the sample split of single calls (model / none / 2-32 ranges); "
+                             "per batch: the kernel assignment (rule / table / all single / "
+                             "all pairs)",
            "batch_kernel_choice": batch_choice,
            "bit_identical_to_separate": bool(same)}
     plan.close()

@@ -406,6 +406,18 @@ int gbmi_tile_n(int64_t m, int64_t n);
 gbmi_status gbmi_tuner_set_pair(int64_t m, int64_t n, int pair);
 int gbmi_tuner_pair(int64_t m, int64_t n);
 
+/* Sample split of the (m, n) bucket's tensor-core Gram when it has fewer
+ * tiles than the GPU runs at once (few variables, many samples): 0 = the
+ * built-in cost model (default), 1 = never split, S in 2..128 = cut the
+ * samples into S ranges whose exact int32 counts are summed by the MI (or
+ * counts) kernel, where S keeps every range at least 2048 samples, at most
+ * 2^24, and the ranges' counts within 2 GB (otherwise the model decides).
+ * GBMI_OPT_SPLIT_K set to 1 or 2 overrides it.  Applies to single calls.
+ * gbmi_tuner_split returns the current value (0 for an untuned bucket).
+ * Errors: GBMI_ERR_ARG. */
+gbmi_status gbmi_tuner_set_split(int64_t m, int64_t n, int parts);
+int gbmi_tuner_split(int64_t m, int64_t n);
+
 /* Per-kernel launch profile (enable with GBMI_OPT_PROFILE).  Each kernel
  * launch is bracketed by CUDA events on the library's stream;
  * gbmi_profile_entries() waits for the recorded launches, folds them into

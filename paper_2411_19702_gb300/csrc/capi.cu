@@ -267,8 +267,10 @@ bool use_pair(const DeviceCtx& c, int64_t m, int64_t n_a, int64_t n_b, bool sym,
 // kernel: about 3 x S x n_a x n_b x 4 bytes at HBM rate); a split is taken
 // only when the model gains at least 10% over one part.  spk: samples per K
 // block (128 FP8, 256 FP4).
+// tuned: the bucket's part count from the tuner table (0: none; 1: no split;
+// S >= 2: S parts, taken where the limits below allow it, else the model).
 int split_parts(int units, int tiles, int64_t kb_total, int64_t n_a, int64_t n_b,
-                int64_t spk = kKbSamplesFp8) {
+                int64_t spk = kKbSamplesFp8, int tuned = 0) {
     const int64_t kMinPartKb = std::max<int64_t>(1, 2048 / spk);   // 2048 samples per part
     constexpr int64_t kMaxParts = 128;
     constexpr int64_t kMaxSliceBytes = int64_t{2} << 30;
@@ -283,6 +285,11 @@ int split_parts(int units, int tiles, int64_t kb_total, int64_t n_a, int64_t n_b
     const double slice = static_cast<double>(n_a) * n_b * 4.0;
     int64_t s_max = std::min(kMaxParts, kb_total / kMinPartKb);
     while (s_max > 1 && s_max * slice > kMaxSliceBytes) --s_max;
+    if (g_opt.split_k != 2 && tuned == 1) return 1;
+    if (g_opt.split_k != 2 && tuned >= 2 && tuned >= exact && tuned <= s_max) {
+        const int64_t kb_s = (kb_total + tuned - 1) / tuned;
+        return static_cast<int>((kb_total + kb_s - 1) / kb_s);
+    }
     if (s_max < std::max<int64_t>(2, exact)) return 1;
     const double t_tile = kBlockSeconds * static_cast<double>(kb_total);
     auto cost = [&](int64_t S) {
@@ -401,7 +408,8 @@ gbmi_status run_gram(DeviceCtx& c, int64_t total_rows, const GramJob& proto, int
     if (dmaps == nullptr && num_shards == 1 && proto.out_t == nullptr &&
         (mode == kTcModeMI || mode == kTcModeCounts)) {
         const int S = split_parts(pair ? c.pair_clusters : c.sm_count, tiles, kb_all,
-                                  proto.n_a, proto.n_b, spk);
+                                  proto.n_a, proto.n_b, spk,
+                                  rt::tuner_split(m, std::max(proto.n_a, proto.n_b)));
         if (S > 1)
             return run_gram_split(c, maps, proto, bn, pair, tiles, kb_all, S, mode, fp4);
     }
@@ -1510,6 +1518,20 @@ int gbmi_tuner_pair(int64_t m, int64_t n) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     if (m < 1 || n < 1) return -1;
     return rt::tuner_pair(m, n);
+}
+
+gbmi_status gbmi_tuner_set_split(int64_t m, int64_t n, int parts) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (m < 1 || n < 1) return fail(GBMI_ERR_ARG, "m and n must be >= 1");
+    if (parts < 0 || parts > 128) return fail(GBMI_ERR_ARG, "parts must be in [0, 128]");
+    rt::tuner_set_split(m, n, parts);
+    return GBMI_OK;
+}
+
+int gbmi_tuner_split(int64_t m, int64_t n) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (m < 1 || n < 1) return 0;
+    return rt::tuner_split(m, n);
 }
 
 int gbmi_tile_n(int64_t m, int64_t n) {

@@ -106,11 +106,14 @@ cudaEvent_t take_event() {
 }
 
 // ---------------------------------------------------------------- tuner table
-// per (m, n) bucket: the single-CTA tile width (0: not tuned) and the kernel
-// (-1: the built-in rule, 0: single-CTA tiles, 1: CTA pairs)
+// per (m, n) bucket: the single-CTA tile width (0: not tuned), the kernel
+// (-1: the built-in rule, 0: single-CTA tiles, 1: CTA pairs) and the sample
+// split of a Gram with fewer tiles than concurrent slots (0: the cost model,
+// 1: no split, S >= 2: S sample ranges where feasible)
 struct TunerEntry {
     int bn = 0;
     int pair = -1;
+    int split = 0;
 };
 std::map<std::pair<int, int>, TunerEntry> g_tuner;
 
@@ -304,6 +307,11 @@ void tuner_set_pair(int64_t m, int64_t n, int pair) { g_tuner[bucket(m, n)].pair
 int tuner_pair(int64_t m, int64_t n) {
     const auto it = g_tuner.find(bucket(m, n));
     return it != g_tuner.end() ? it->second.pair : -1;
+}
+void tuner_set_split(int64_t m, int64_t n, int parts) { g_tuner[bucket(m, n)].split = parts; }
+int tuner_split(int64_t m, int64_t n) {
+    const auto it = g_tuner.find(bucket(m, n));
+    return it != g_tuner.end() ? it->second.split : 0;
 }
 void tuner_clear() { g_tuner.clear(); }
 int tuner_size() { return static_cast<int>(g_tuner.size()); }

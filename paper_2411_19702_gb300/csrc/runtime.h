@@ -114,6 +114,10 @@ void tuner_set(int64_t m, int64_t n, int bn);
 // single-CTA tiles, 1 CTA pairs.
 void tuner_set_pair(int64_t m, int64_t n, int pair);
 int tuner_pair(int64_t m, int64_t n);
+// Sample split of the bucket of (m, n): 0 the cost model (untuned), 1 no
+// split, S >= 2 sample ranges.
+void tuner_set_split(int64_t m, int64_t n, int parts);
+int tuner_split(int64_t m, int64_t n);
 void tuner_clear();
 int tuner_size();
 

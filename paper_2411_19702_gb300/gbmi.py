@@ -81,6 +81,8 @@ def load(path: str | None = None):
             "gbmi_tuner_set": [i64, i64, i32],
             "gbmi_tuner_set_pair": [i64, i64, i32],
             "gbmi_tuner_pair": [i64, i64],
+            "gbmi_tuner_set_split": [i64, i64, i32],
+            "gbmi_tuner_split": [i64, i64],
             "gbmi_tuner_clear": [],
             "gbmi_tile_n": [i64, i64],
             "gbmi_batch_create": [vp, i32, vp],
@@ -540,6 +542,15 @@ def tuner_set_pair(m: int, n: int, pair: int):
 
 def tuner_pair(m: int, n: int) -> int:
     return int(load().gbmi_tuner_pair(int(m), int(n)))
+
+
+def tuner_set_split(m: int, n: int, parts: int):
+    """Sample split for the (m, n) bucket: 0 the cost model, 1 none, S >= 2 ranges."""
+    _check(load().gbmi_tuner_set_split(int(m), int(n), int(parts)))
+
+
+def tuner_split(m: int, n: int) -> int:
+    return int(load().gbmi_tuner_split(int(m), int(n)))
 
 
 def tile_n(m: int, n: int) -> int:

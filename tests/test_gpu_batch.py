@@ -97,6 +97,10 @@ def test_autotuner_installs_choices_and_keeps_results():
         assert set(entry["ms"]) == {"single64", "single128", "single256", "pair"}
         assert gbmi.tile_n(entry["m"], entry["n"]) == entry["tile_n"]
         assert gbmi.tuner_pair(entry["m"], entry["n"]) == entry["pair"]
+        # both buckets are narrow enough for the sample split to be timed
+        assert set(entry["ms_split"]) == {str(p) for p in autotune.SPLITS}
+        assert entry["split"] in autotune.SPLITS
+        assert gbmi.tuner_split(entry["m"], entry["n"]) == entry["split"]
     X = _rand(4000, 96, 7)
     Y = _rand(20000, 900, 8)
     got, goty = gbmi.mi_all_pairs(X, path="fused"), gbmi.mi_all_pairs(Y, path="fused")
@@ -114,6 +118,31 @@ def test_autotuner_installs_choices_and_keeps_results():
     assert torch.equal(goty, refy)
     assert torch.equal(bx, ref) and torch.equal(by, refy)
     b.close()
+
+
+@pytest.mark.parametrize("parts", [1, 2, 5, 16])
+def test_tuned_sample_split_keeps_results(parts):
+    # few variables, many samples: a call the cost model may split; a tuned
+    # part count must give the same bits as no split at all
+    X = _rand(200_000, 200, 3)
+    gbmi.set_option(gbmi.OPT_SPLIT_K, 1)
+    try:
+        ref = gbmi.mi_all_pairs(X, path="fused")
+        refc = gbmi.counts_all_pairs(X, path="plain")
+    finally:
+        gbmi.set_option(gbmi.OPT_SPLIT_K, 0)
+    gbmi.tuner_set_split(200_000, 200, parts)
+    try:
+        gbmi.profile(enable=True, reset=True)
+        got = gbmi.mi_all_pairs(X, path="fused")
+        gotc = gbmi.counts_all_pairs(X, path="plain")
+        prof = gbmi.profile(enable=False)
+    finally:
+        gbmi.tuner_clear()
+    gbmi.sync()
+    assert torch.equal(got, ref) and torch.equal(gotc, refc)
+    split = prof.get("gram_tc_split_counts", {}).get("launches", 0) > 0
+    assert split == (parts > 1), prof
 
 
 def test_batch_on_cta_pairs_matches_single_calls():

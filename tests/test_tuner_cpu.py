@@ -58,9 +58,10 @@ def test_autotune_table_round_trip(tmp_path):
     table = {"16,26": {"m": 100_000, "n": 10_000, "tile_n": 128, "pair": 1,
                        "ms": {"single64": 3.0, "single128": 2.0, "single256": 2.5,
                               "pair": 1.5}},
-             "12,12": {"m": 5000, "n": 64, "tile_n": 64, "pair": 0,
+             "12,12": {"m": 5000, "n": 64, "tile_n": 64, "pair": 0, "split": 8,
                        "ms": {"single64": 0.1, "single128": 0.2, "single256": 0.3,
-                              "pair": 0.4}}}
+                              "pair": 0.4},
+                       "ms_split": {"0": 0.05, "1": 0.1, "8": 0.04}}}
     path = str(tmp_path / "tune.json")
     autotune.save(table, path)
     gbmi.tuner_clear()
@@ -70,9 +71,24 @@ def test_autotune_table_round_trip(tmp_path):
     assert gbmi.tuner_pair(100_000, 10_000) == 1
     assert gbmi.tuner_pair(5000, 64) == 0
     assert gbmi.tuner_pair(5000, 5000) == -1          # untuned bucket: the built-in rule
+    assert gbmi.tuner_split(5000, 64) == 8
+    assert gbmi.tuner_split(100_000, 10_000) == 0     # no split entry: the cost model
     assert autotune.bucket(100_000, 10_000) == (16, 26)
     gbmi.tuner_clear()
     assert gbmi.tuner_pair(100_000, 10_000) == -1
+
+
+def test_tuner_split_argument_checks():
+    for bad in (-1, 129):
+        with pytest.raises(gbmi.GbmiError):
+            gbmi.tuner_set_split(1000, 100, bad)
+    with pytest.raises(gbmi.GbmiError):
+        gbmi.tuner_set_split(0, 100, 2)
+    gbmi.tuner_set_split(1000, 100, 4)
+    assert gbmi.tuner_split(1000, 100) == 4
+    assert gbmi.tuner_split(1000, 100_000) == 0
+    gbmi.tuner_clear()
+    assert gbmi.tuner_split(1000, 100) == 0
 
 
 def test_tuner_pair_argument_checks():
