@@ -125,13 +125,14 @@ constexpr int kQ = 8;                            // tile-id queue between the ro
 // full, empty, tmem full x2, tmem empty x2, drain, queue full x kQ, queue empty x kQ
 constexpr int kNumBarsFor(int stages) { return 2 * stages + 4 + 1 + 2 * kQ; }
 
-// Pipeline stages of a kernel: single CTA 4; CTA pairs 6, except the kernel
-// with the FP64 combine, which takes 5: its epilogue waits on reads scattered
-// over the n log2 n table, and the stage it gives up leaves L1 twice the room
-// (measured at 10^5 x 10^4: its Gram 2.41 -> 1.92 ms, while the FP32 epilogue
-// kernel is slower with fewer than 6).
+// Pipeline stages of a kernel: single CTA 4, CTA pairs 6, one fewer for the
+// kernels with the FP64 combine: their epilogue waits on reads scattered over
+// the n log2 n table, and the stage they give up drops shared memory to the
+// next carveout, leaving L1 about 60 KB instead of 28 (measured at 10^5 x
+// 10^4: the pair Gram 2.41 -> 1.92 ms, the single-CTA one 2.87 -> 2.27 ms,
+// while the FP32 epilogue kernels are slower with fewer stages).
 __host__ __device__ constexpr int stages_for(int mode, bool pair) {
-    return !pair ? 4 : (mode == kTcModeMI ? 5 : 6);
+    return mode == kTcModeMI ? (pair ? 5 : 3) : (pair ? 6 : 4);
 }
 
 // Shared-memory plan.  Single CTA: kSt stages of A (128 rows) + B (up to 256
@@ -1118,20 +1119,23 @@ gram_tc_kernel(const __grid_constant__ OperandMaps maps, const __grid_constant__
 
 template <bool kPair>
 cudaError_t set_smem_attrs() {
-    const int bytes = static_cast<int>(Plan<kPair>::smem_bytes);
+    // each mode's kernel: its own plan's shared memory (stages_for)
     cudaError_t e;
     e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI, kPair>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(Plan<kPair, stages_for(kTcModeMI, kPair)>::smem_bytes));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeMI32, kPair>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(Plan<kPair, stages_for(kTcModeMI32, kPair)>::smem_bytes));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(gram_tc_kernel<kTcModeCounts, kPair>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(Plan<kPair, stages_for(kTcModeCounts, kPair)>::smem_bytes));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(gram_tc_kernel<kTcModeCountsAdd, kPair>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(
+        gram_tc_kernel<kTcModeCountsAdd, kPair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        static_cast<int>(Plan<kPair, stages_for(kTcModeCountsAdd, kPair)>::smem_bytes));
 }
 
 template <int kMode>
@@ -1233,19 +1237,23 @@ cudaError_t launch_gram_tc(const OperandMaps& maps, const GramLaunch& L, int gri
             default: return cudaErrorInvalidValue;
         }
     }
-    constexpr size_t kSmem = Plan<false>::smem_bytes;
+    // each mode's kernel takes its own plan's shared memory (stages_for)
     switch (mode) {
         case kTcModeMI32:
-            gram_tc_kernel<kTcModeMI32, false><<<grid, threads_of(kTcModeMI32), kSmem, s>>>(maps, L);
+            gram_tc_kernel<kTcModeMI32, false><<<grid, threads_of(kTcModeMI32),
+                Plan<false, stages_for(kTcModeMI32, false)>::smem_bytes, s>>>(maps, L);
             break;
         case kTcModeMI:
-            gram_tc_kernel<kTcModeMI, false><<<grid, threads_of(kTcModeMI), kSmem, s>>>(maps, L);
+            gram_tc_kernel<kTcModeMI, false><<<grid, threads_of(kTcModeMI),
+                Plan<false, stages_for(kTcModeMI, false)>::smem_bytes, s>>>(maps, L);
             break;
         case kTcModeCounts:
-            gram_tc_kernel<kTcModeCounts, false><<<grid, threads_of(kTcModeCounts), kSmem, s>>>(maps, L);
+            gram_tc_kernel<kTcModeCounts, false><<<grid, threads_of(kTcModeCounts),
+                Plan<false, stages_for(kTcModeCounts, false)>::smem_bytes, s>>>(maps, L);
             break;
         case kTcModeCountsAdd:
-            gram_tc_kernel<kTcModeCountsAdd, false><<<grid, threads_of(kTcModeCountsAdd), kSmem, s>>>(maps, L);
+            gram_tc_kernel<kTcModeCountsAdd, false><<<grid, threads_of(kTcModeCountsAdd),
+                Plan<false, stages_for(kTcModeCountsAdd, false)>::smem_bytes, s>>>(maps, L);
             break;
         default:
             return cudaErrorInvalidValue;
