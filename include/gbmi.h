@@ -418,6 +418,15 @@ int gbmi_tuner_pair(int64_t m, int64_t n);
 gbmi_status gbmi_tuner_set_split(int64_t m, int64_t n, int parts);
 int gbmi_tuner_split(int64_t m, int64_t n);
 
+/* The tail plan a tensor-core launch of `tiles` tiles on `units` concurrent
+ * tile slots would use under the current GBMI_OPT_TAIL_COLS: returns how many
+ * tiles at the end of its list run as column shares (0: none) and stores the
+ * shares per tile in *parts (if not null).  Automatic mode splits the last
+ * partial wave (tiles mod units) into the 2-4 shares that fill the fewest
+ * share-length waves, and nothing when that would not end before a whole-tile
+ * wave.  A planning query: it launches nothing and needs no GPU. */
+int gbmi_tail_cols_plan(int tiles, int units, int* parts);
+
 /* Per-kernel launch profile (enable with GBMI_OPT_PROFILE).  Each kernel
  * launch is bracketed by CUDA events on the library's stream;
  * gbmi_profile_entries() waits for the recorded launches, folds them into

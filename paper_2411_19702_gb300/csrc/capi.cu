@@ -1534,6 +1534,14 @@ int gbmi_tuner_split(int64_t m, int64_t n) {
     return rt::tuner_split(m, n);
 }
 
+int gbmi_tail_cols_plan(int tiles, int units, int* parts) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    int p = 0;
+    const int S = tail_cols_plan(tiles, units, &p);
+    if (parts != nullptr) *parts = p;
+    return S;
+}
+
 int gbmi_tile_n(int64_t m, int64_t n) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     if (m < 1 || n < 1) return 0;

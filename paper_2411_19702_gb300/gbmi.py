@@ -83,6 +83,7 @@ def load(path: str | None = None):
             "gbmi_tuner_pair": [i64, i64],
             "gbmi_tuner_set_split": [i64, i64, i32],
             "gbmi_tuner_split": [i64, i64],
+            "gbmi_tail_cols_plan": [i32, i32, vp],
             "gbmi_tuner_clear": [],
             "gbmi_tile_n": [i64, i64],
             "gbmi_batch_create": [vp, i32, vp],
@@ -551,6 +552,13 @@ def tuner_set_split(m: int, n: int, parts: int):
 
 def tuner_split(m: int, n: int) -> int:
     return int(load().gbmi_tuner_split(int(m), int(n)))
+
+
+def tail_cols_plan(tiles: int, units: int) -> tuple[int, int]:
+    """(tiles split into column shares, shares per tile) for a launch of `tiles` on `units` slots."""
+    parts = ctypes.c_int(0)
+    S = int(load().gbmi_tail_cols_plan(int(tiles), int(units), ctypes.byref(parts)))
+    return S, int(parts.value)
 
 
 def tile_n(m: int, n: int) -> int:

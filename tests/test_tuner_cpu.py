@@ -169,3 +169,20 @@ def test_environment_sets_option_defaults_and_logging():
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))), timeout=120)
     assert r.stdout.strip() != "100" and r.returncode == 0
+
+
+def test_tail_cols_plan():
+    # automatic: the last partial wave (tiles mod units) in the 2-4 shares that
+    # fill the fewest share-length waves; nothing when no plan ends sooner
+    gbmi.set_option(gbmi.OPT_TAIL_COLS, 1)
+    assert gbmi.tail_cols_plan(865, 76) == (29, 2)    # 10^4 variables on 76 CTA pairs
+    assert gbmi.tail_cols_plan(100, 76) == (24, 3)    # 72 thirds: one third-length wave
+    assert gbmi.tail_cols_plan(152, 76) == (0, 0)     # no partial wave
+    assert gbmi.tail_cols_plan(50, 76) == (0, 0)      # fewer tiles than slots
+    assert gbmi.tail_cols_plan(140, 76) == (0, 0)     # 64 left: every plan takes a whole wave
+    assert gbmi.tail_cols_plan(0, 76) == (0, 0)
+    gbmi.set_option(gbmi.OPT_TAIL_COLS, 3)            # forced: every tile in 3 shares
+    assert gbmi.tail_cols_plan(865, 76) == (865, 3)
+    gbmi.set_option(gbmi.OPT_TAIL_COLS, 0)            # off
+    assert gbmi.tail_cols_plan(865, 76) == (0, 0)
+    gbmi.set_option(gbmi.OPT_TAIL_COLS, 1)
